@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Throughput of the fused B-TriRT sweep on the 2048 x 1024 production cavity.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one fused collide-and-stream sweep (pull streaming with the wall
+rules, H -> (T, f_l) inversion, g and f block collisions, buoyancy, the
+per-step heated-wall inflow reduction) over the whole 2048 x 1024 lattice in
+FP32; the FP64 diagnostics reductions (melt fraction, sum H, max |u|, NaN
+flag) are fused into every 100th sweep, the cadence of the melt-fraction and
+Nusselt history.  Metric: MLUPS (million lattice-cell updates per second; one
+update advances both f and g of one cell).  The working set (2 x 151 MB of
+populations) is larger than L2, so no flush is needed between steps.
+
+For N > 1 (torchrun) every rank advances its own cavity (replicas: the method
+needs no exchange between independent solves); value = all cells updated by
+all ranks / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on this host's cores, one full
+oracle step of the same workload per step, and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 2048, 1024
+BYTES_PER_LUP = {"fp32": 144, "fp64": 288}   # 18 populations read + 18 written
+DIAG_EVERY = 100
+METRIC = "MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "sweep_fp32_cavity_2048x1024.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_13086_gb300", "csrc", f)
+                  for f in ("sweep.cuh", "lbm_internal.h")]
+
+
+def workload_config(precision: str) -> dict:
+    return {"workload": f"cavity {NX}x{NY}, Ra 1e8, Pr 1, Ste 1, Ma 0.1, strip W/4 centred, "
+                        f"{precision.upper()} populations",
+            "nx": NX, "ny": NY, "precision": precision,
+            "diagnostics": f"fused every {DIAG_EVERY} steps; heated-wall flux every step",
+            "l2": "inputs larger than L2 (2 x 151 MB populations), no flush"}
+
+
+# ------------------------------------------------------------ distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_group(ws: int, backend: str):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def aggregate(elapsed_s: float, units: float, dist, device=None) -> tuple[float, float]:
+    """Max of the per-rank times and sum of the per-rank units."""
+    if dist is None:
+        return elapsed_s, units
+    import torch
+
+    t = torch.tensor([elapsed_s, units], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
+# ------------------------------------------------------------ measurement aids
+def measured_peak_gbs() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if key in d:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic() -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    m_traf = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_traf or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_traf.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle arm
+def oracle_mlups(steps: int, warmup: int, threads: int) -> tuple[float, float, int]:
+    """Time the FP64 oracle on the same workload: returns (MLUPS, seconds, steps)."""
+    from oracle import oracle as O
+    from paper_1909_13086_gb300 import workloads
+
+    nx, ny, p = workloads.cavity_2048x1024()
+    o = O.Oracle(nx, ny, threads=threads, **p)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e6, dt, steps
+
+
+def cpu_baseline_sample(threads: int) -> dict:
+    """A bounded sample (about 10-20 s) of the oracle on this host."""
+    from oracle import oracle as O
+
+    O.build()
+    # one step first, to size the sample
+    rate1, dt1, _ = oracle_mlups(1, 0, threads)
+    steps = max(2, min(200, int(12.0 / max(dt1, 1e-3))))
+    rate, dt, n = oracle_mlups(steps, 0, threads)
+    return {"value": round(rate, 3), "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"{n} FP64 oracle steps of the {NX}x{NY} cavity ({dt:.1f} s, "
+                      f"{threads} OpenMP threads)"}
+
+
+def run_reference(args) -> None:
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    O.build()
+    threads = os.cpu_count() or 1
+    rate, dt, n = oracle_mlups(args.steps, args.warmup, threads)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(rate, 3), "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config("fp64"),
+        "cpu_baseline": {"value": round(rate, 3), "unit": METRIC, "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"{n} full FP64 oracle steps of the {NX}x{NY} cavity"},
+        "e2e": {"value": round(rate, 3), "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measure_e2e(args, lat, p, prec, stream, dist, local) -> dict:
+    """End to end through the C ABI with host buffers: write the state from
+    pinned host memory, step, read each step's diagnostics record, read the
+    final fields back."""
+    import torch
+
+    from paper_1909_13086_gb300 import lbm
+
+    nx, ny = lat.nx, lat.ny
+    cells = nx * ny
+    f0, g0, _ = lat.populations()
+    e2e_lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream.cuda_stream)
+    lbm.lbm_set_diag_every(e2e_lat.h, 1)
+    f_host = torch.from_numpy(f0).pin_memory().numpy()
+    g_host = torch.from_numpy(g0).pin_memory().numpy()
+    out = {k: torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy()
+           for k in ("H", "T", "fl", "ux", "uy", "rho")}
+    e2e_steps = max(1, args.steps)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_lat.set_populations(f_host, g_host, 0)
+    for _ in range(e2e_steps):
+        e2e_lat.step(1)
+        e2e_lat.diagnostics()
+    lbm.lbm_read_fields(e2e_lat.h, 63, *[out[k] for k in ("H", "T", "fl", "ux", "uy", "rho")])
+    t_e2e = time.perf_counter() - t0
+    t_e2e_max, e2e_units = aggregate(t_e2e, float(cells * e2e_steps), dist,
+                                     device=torch.device("cuda", local))
+    h2d = f_host.nbytes + g_host.nbytes
+    d2h = 80 * e2e_steps + sum(a.nbytes for a in out.values())
+    e2e_lat.close()
+
+    return {"value": round(e2e_units / t_e2e_max / 1e6, 1), "unit": METRIC,
+            "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
+            "steps": e2e_steps,
+            "path": "lbm_write_populations (pinned host FP64) + lbm_step(1) + lbm_diagnostics per "
+                    "step + lbm_read_fields(all)"}
+
+
+# ------------------------------------------------------------ GPU arm
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+
+    from paper_1909_13086_gb300 import lbm, workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_group(ws, "nccl")
+    # A dedicated (non-default) stream: the library enqueues on it and the
+    # CUDA events below are recorded on it.
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    nx, ny, p = workloads.cavity_2048x1024()
+    prec = args.precision
+    cells = nx * ny
+
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream.cuda_stream)
+    lbm.lbm_set_diag_every(lat.h, DIAG_EVERY)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing: K sweeps, inputs already in HBM
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        lat.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = start.elapsed_time(stop) / 1e3
+    t_max, units = aggregate(elapsed, float(cells * args.steps), dist,
+                             device=torch.device("cuda", local))
+    value = units / t_max / 1e6
+    d = lat.diagnostics()
+    assert d["nan_flag"] == 0
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, lat, p, prec, stream, dist, local)
+
+    # ---- roofline of the sweep (the only kernel in the timed region)
+    peak, peak_kind = measured_peak_gbs()
+    kernel_s = elapsed / args.steps
+    alg_bytes = BYTES_PER_LUP[prec] * cells
+    achieved = alg_bytes / kernel_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": workload_config(prec),
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks.summary(),
+        "melt_fraction": d["melt_fraction"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(os.cpu_count() or 1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

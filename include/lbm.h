@@ -1,0 +1,185 @@
+/*
+ * lbm.h -- C ABI of the GB300 B-TriRT melting solver.
+ *
+ * One fused CUDA sweep per time step advances, on one GPU, the D2Q9 lattice of
+ * the paper "Lattice Boltzmann simulations of melting in a rectangular cavity
+ * heated locally from below at high Rayleigh number" (Zhao, Wu, Chai, Shi):
+ *   - the total-enthalpy populations g_i with the block triple-relaxation-time
+ *     (B-TriRT) collision of Eq. 2 and the equilibrium of Eq. 4, k1 from the
+ *     thermal diffusivity by Eq. 5, optionally k2 = 2 - k1 (Eq. 6);
+ *   - the per-cell inversion H -> (T, f_l) of H = C_p T + f_l L (Eq. 1);
+ *   - the flow populations f_i with Boussinesq buoyancy and the liquid-fraction
+ *     velocity suppression u = f_l u* (readings of Sec. 3.2, which cites its
+ *     flow model without stating it);
+ *   - pull streaming with half-way bounce-back (no-slip, adiabatic) and
+ *     anti-bounce-back on the wall held at T_h (Sec. 3.1 left wall, Sec. 3.2
+ *     heated strip of width D centred at C on the bottom wall).
+ * Lattice units throughout: dx = dt = 1, c_s^2 = 1/3, C_p = rho0 = 1, T_m = 0,
+ * T_h = 1.
+ *
+ * Conventions
+ *   - Every call returns an int status: LBM_OK (0) or a negative LBM_ERR_*.
+ *     lbm_last_error(h) gives a message (h may be NULL for create failures).
+ *     No call throws or aborts.
+ *   - The handle owns its device memory (allocated through the allocator hook
+ *     if one is installed, else cudaMalloc).  Host arrays are owned by the
+ *     caller and only read or written during the call.
+ *   - Host field and population arrays are row-major FP64: cell (x, y) at index
+ *     y*nx + x, 0 <= x < nx (width), 0 <= y < ny (height, y = 0 at the bottom
+ *     wall).  Population arrays are plane-major: direction i (0..8) at offset
+ *     i*nx*ny.  D2Q9 order: c_0 = (0,0), c_1 = (1,0), c_2 = (0,1), c_3 = (-1,0),
+ *     c_4 = (0,-1), c_5 = (1,1), c_6 = (-1,1), c_7 = (-1,-1), c_8 = (1,-1).
+ *   - Work is enqueued on the handle's CUDA stream (borrowed from the caller,
+ *     or created by the library when NULL is passed).  Calls that return data
+ *     to the host synchronise that stream.
+ *   - One handle must not be used from two host threads at the same time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_s *lbm_handle;
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument or parameter set                */
+    LBM_ERR_OOM = -2,      /* device or host allocation failed                 */
+    LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                       */
+    LBM_ERR_DIVERGED = -4, /* a non-finite H or rho was found by the diagnostics */
+    LBM_ERR_STATE = -5,    /* call not valid in the handle's current state     */
+    LBM_ERR_TIMEOUT = -6   /* reserved: a bounded device wait ran out          */
+};
+
+/* Storage and arithmetic precision of the populations. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+
+/* Problem kind. */
+enum {
+    LBM_CAVITY = 0, /* Sec. 3.2: closed cavity, heated strip on the bottom wall  */
+    LBM_STEFAN = 1  /* Sec. 3.1: left wall at T_h, right wall adiabatic, y periodic */
+};
+
+/* Problem parameters (Sec. 3.1, Sec. 3.2 and Eqs. 5-6). */
+typedef struct {
+    int problem;            /* LBM_CAVITY or LBM_STEFAN                                 */
+    double Ra, Pr, Ste, Ma; /* Rayleigh, Prandtl, Stefan and Mach numbers.  Cavity units:
+                               U = Ma c_s, nu = U ny sqrt(Pr/Ra), alpha = nu/Pr,
+                               g beta = U^2/ny; L = 1/Ste                                */
+    double strip_center;    /* C, heated-strip centre as a fraction of the width         */
+    double strip_width;     /* D, heated-strip width as a fraction of the width; 0 = none */
+    double k0, k2;          /* g rates of Eq. 2 in (0, 2); k2 < 0 selects k2 = 2 - k1    */
+    double alpha_override;  /* > 0: thermal diffusivity alpha directly (nu = Pr alpha,
+                               g beta from Ra); 0: from Ra, Pr, Ma; < 0 is rejected      */
+    double k0f, k1f;        /* flow ghost and first-moment rates in (0, 2); the second-
+                               moment rate is 1/(nu/c_s^2 + 1/2)                         */
+    int flow_on;            /* 0: u = 0 and f is not evolved (Sec. 3.1 conduction)       */
+    double init_amp;        /* amplitude a of the initial perturbation: H0 = a (2r - 1),
+                               r = (splitmix64(seed xor (y nx + x)) >> 11) 2^-53          */
+    uint64_t seed;
+} lbm_params;
+
+/* Parameters derived by lbm_set_params (lattice units). */
+typedef struct {
+    double nu, alpha, gbeta;
+    double k0, k1, k2;       /* k1 from Eq. 5: 1/k1 = alpha/c_s^2 + 1/2                 */
+    double k0f, k1f, k2f;
+    double Lh;               /* latent heat 1/Ste                                        */
+    double a, b;             /* heated segment [a, b] of the bottom wall, in cells       */
+    double Href;             /* reference length: ny (cavity) or nx (Stefan)             */
+    double heated_len;       /* b - a (cavity) or ny (Stefan)                            */
+} lbm_derived;
+
+/* Diagnostics of the current step, accumulated in FP64 on the device. */
+typedef struct {
+    long long step;          /* steps taken since lbm_set_params                        */
+    double melt_fraction;    /* sum f_l / (nx ny)                                        */
+    double H_total;          /* sum H                                                    */
+    double Q_strip;          /* enthalpy entering through the T_h wall in the last step:
+                                sum over heated crossings of 2 w_i T_h - 2 g*_opp(i)     */
+    double Q_cum;            /* Q_strip summed over all steps since lbm_set_params       */
+    double Nu;               /* Q_strip Href / (alpha dT heated_len)                     */
+    double front_x;          /* sum f_l / ny: melt-front distance from x = 0 (Stefan)    */
+    double max_u;            /* max |u|                                                  */
+    int nan_flag;            /* 1 if any H or rho was not finite                         */
+} lbm_diag;
+
+/* Create a solver for an nx x ny lattice (nx, ny >= 2) in the given precision.
+ * cuda_stream: a cudaStream_t to borrow, or NULL for a library-owned
+ * non-blocking stream (NULL is never taken to mean the legacy default stream).
+ * Limits: ny <= 65535, nx * ny <= 2^31.
+ * Allocates the two population buffers (2 x 18 planes).  State is undefined
+ * until lbm_set_params.  Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out);
+
+/* Validate and derive the parameters (Eqs. 5-6 and the unit mapping above),
+ * then reset the state to step 0: f_i = w_i, g_i = g_eq(H0, T(H0), u = 0)
+ * (Eq. 4).  Errors: LBM_ERR_ARG (rates outside (0, 2), Ste <= 0, ...). */
+int lbm_set_params(lbm_handle h, const lbm_params *p);
+
+/* Copy the derived parameters.  Error LBM_ERR_STATE before lbm_set_params. */
+int lbm_get_derived(lbm_handle h, lbm_derived *out);
+
+/* Advance n >= 0 time steps (one fused sweep each), asynchronously on the
+ * stream.  The diagnostics reductions are fused into the last sweep (and into
+ * every diag_every-th sweep, see lbm_set_diag_every).  Errors: LBM_ERR_ARG,
+ * LBM_ERR_STATE (no parameters), LBM_ERR_CUDA. */
+int lbm_step(lbm_handle h, long long n);
+
+/* Fuse the diagnostics into every k-th sweep as well (k = 0: last sweep of
+ * each lbm_step call only, the default). */
+int lbm_set_diag_every(lbm_handle h, long long k);
+
+/* Bit mask selecting the fields of lbm_read_fields. */
+enum { LBM_FIELD_H = 1, LBM_FIELD_T = 2, LBM_FIELD_FL = 4, LBM_FIELD_UX = 8,
+       LBM_FIELD_UY = 16, LBM_FIELD_RHO = 32, LBM_FIELD_ALL = 63 };
+
+/* Macroscopic fields of the current step n: the H, T, f_l, u (= f_l u*) and rho
+ * computed inside step n from the streamed populations (at n = 0: the initial
+ * fields, u = 0).  Each selected pointer receives nx*ny doubles; unselected or
+ * NULL pointers are skipped.  Synchronises.  Errors: LBM_ERR_STATE right after
+ * lbm_write_populations (no step taken yet), LBM_ERR_CUDA. */
+int lbm_read_fields(lbm_handle h, unsigned mask, double *H, double *T, double *fl,
+                    double *ux, double *uy, double *rho);
+
+/* Diagnostics record of the current step.  Synchronises.  Returns
+ * LBM_ERR_DIVERGED (with *out filled) if nan_flag is set. */
+int lbm_diagnostics(lbm_handle h, lbm_diag *out);
+
+/* Checkpoint: the current post-collision populations (9*nx*ny doubles each
+ * for f and g, plane-major) and the step counter.  Synchronises. */
+int lbm_read_populations(lbm_handle h, double *f, double *g, long long *step);
+
+/* Resume: overwrite the populations (rounded to the handle's precision) and
+ * the step counter; Q_cum restarts at 0.  Fields and diagnostics are
+ * undefined until the next step. */
+int lbm_write_populations(lbm_handle h, const double *f, const double *g, long long step);
+
+/* Free the handle's device memory (and its stream, if library-owned). */
+int lbm_destroy(lbm_handle h);
+
+/* Message of the last error on h (or of the calling thread's last create
+ * failure when h is NULL).  Never NULL. */
+const char *lbm_last_error(lbm_handle h);
+
+/* Optional device allocator hook, used by every later lbm_create (e.g. to take
+ * memory from a framework's caching allocator).  alloc returns a device
+ * pointer of at least `bytes` bytes aligned to 256 B, or NULL; release frees
+ * it.  Pass NULL, NULL to restore cudaMalloc/cudaFree.  Not thread-safe
+ * against concurrent lbm_create calls. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, void *ctx);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *ctx);
+
+/* Library build identification: "btrirt <version> sm_103a". */
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,509 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// Owns the device buffers of one lattice, derives the parameters (Eq. 5 for
+// k1, Eq. 6 on request for k2, and the cavity unit mapping), and enqueues the
+// sweep kernels on the handle's stream.  No torch types cross this boundary:
+// a framework can lend its stream (cuda_stream) and its allocator
+// (lbm_set_allocator).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace btrirt;
+
+namespace {
+
+thread_local char g_create_error[256] = "";
+
+lbm_alloc_fn g_alloc = nullptr;
+lbm_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+
+constexpr int kBlockX = 256;  // threads along x per block (8 warps)
+constexpr int kBlockY = 1;
+
+}  // namespace
+
+struct lbm_s {
+    int nx = 0, ny = 0, precision = LBM_FP32, device = 0;
+    size_t esize = 4;           // bytes per population value
+    int pitch = 0;              // row pitch, elements
+    long long pstride = 0;      // plane stride, elements
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *buf[2] = {nullptr, nullptr};  // 18 planes each
+    int cur = 0;                // buffer holding the current post-collision populations
+    bool has_prev = false;      // buf[cur ^ 1] holds the previous step's populations
+    long long step = 0;
+    long long diag_every = 0;
+    bool params_set = false;
+    lbm_params p{};
+    lbm_derived d{};
+    int lo2 = 0, hi2 = -1, strip_on = 0;
+    dim3 block, grid;
+    // scratch: reduction partials, tickets, record; allocated once
+    void *scratch = nullptr;
+    double *qpart = nullptr, *dpart = nullptr;
+    unsigned *counters = nullptr;
+    DevRecord *rec = nullptr;
+    int nq = 0;
+    // field output staging (6 x nx*ny doubles), allocated on first use
+    double *fields = nullptr;
+    // allocator used for this handle's memory
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn release = nullptr;
+    void *alloc_ctx = nullptr;
+    char err[256] = "";
+};
+
+namespace {
+
+int set_err(lbm_s *h, int code, const char *fmt, ...) {
+    char *dst = h ? h->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return set_err((h), LBM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+void *dev_alloc(lbm_s *h, size_t bytes) {
+    if (h->alloc) return h->alloc(bytes, h->alloc_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(lbm_s *h, void *p) {
+    if (!p) return;
+    if (h->release)
+        h->release(p, h->alloc_ctx);
+    else
+        cudaFree(p);
+}
+
+size_t buffer_bytes(const lbm_s *h) { return (size_t)18 * (size_t)h->pstride * h->esize; }
+
+template <typename real>
+SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
+    SweepArgs<real> a{};
+    a.src = static_cast<const real *>(src);
+    a.dst = static_cast<real *>(dst);
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.pstride = h->pstride;
+    a.k0 = (real)h->d.k0;
+    a.k1 = (real)h->d.k1;
+    a.k2 = (real)h->d.k2;
+    a.k0f = (real)h->d.k0f;
+    a.k1f = (real)h->d.k1f;
+    a.k2f = (real)h->d.k2f;
+    a.Lh = (real)h->d.Lh;
+    a.gbeta = (real)h->d.gbeta;
+    a.strip_on = h->strip_on;
+    a.lo2 = h->lo2;
+    a.hi2 = h->hi2;
+    a.qpart = h->qpart;
+    a.qcount = h->counters;
+    a.nq = h->nq;
+    a.dpart = h->dpart;
+    a.dcount = h->counters + 1;
+    a.rec = h->rec;
+    a.step = h->step;
+    return a;
+}
+
+// Validate p and fill d (same mapping as documented in lbm.h).
+int derive(lbm_s *h, const lbm_params *p, lbm_derived *d) {
+    const double cs2 = 1.0 / 3.0, dT = 1.0;
+    if (p->problem != LBM_CAVITY && p->problem != LBM_STEFAN)
+        return set_err(h, LBM_ERR_ARG, "problem must be LBM_CAVITY or LBM_STEFAN");
+    if (!(p->Ste > 0.0)) return set_err(h, LBM_ERR_ARG, "Ste must be > 0");
+    if (!(p->alpha_override >= 0.0))
+        return set_err(h, LBM_ERR_ARG, "alpha_override must be >= 0");
+    std::memset(d, 0, sizeof(*d));
+    d->Href = p->problem == LBM_CAVITY ? (double)h->ny : (double)h->nx;
+    if (p->alpha_override > 0.0) {
+        d->alpha = p->alpha_override;
+        d->nu = (p->Pr > 0.0 ? p->Pr : 1.0) * d->alpha;
+        d->gbeta = p->Ra > 0.0 ? p->Ra * d->nu * d->alpha / (dT * d->Href * d->Href * d->Href) : 0.0;
+    } else {
+        if (!(p->Ra > 0.0 && p->Pr > 0.0 && p->Ma > 0.0))
+            return set_err(h, LBM_ERR_ARG, "Ra, Pr and Ma must be > 0 (or set alpha_override)");
+        const double U = p->Ma * std::sqrt(cs2);
+        d->nu = U * d->Href * std::sqrt(p->Pr / p->Ra);
+        d->alpha = d->nu / p->Pr;
+        d->gbeta = U * U / (dT * d->Href);
+    }
+    d->k1 = 1.0 / (d->alpha / cs2 + 0.5);  // Eq. 5, dt = 1
+    d->k0 = p->k0;
+    d->k2 = p->k2 < 0.0 ? 2.0 - d->k1 : p->k2;  // Eq. 6 on request
+    d->k0f = p->k0f;
+    d->k1f = p->k1f;
+    d->k2f = 1.0 / (d->nu / cs2 + 0.5);
+    d->Lh = dT / p->Ste;
+    if (p->problem == LBM_CAVITY) {
+        if (!(p->strip_width >= 0.0 && p->strip_center >= 0.0 && p->strip_center <= 1.0))
+            return set_err(h, LBM_ERR_ARG, "strip centre must be in [0, 1] and width >= 0");
+        d->a = h->nx * (p->strip_center - 0.5 * p->strip_width);
+        d->b = h->nx * (p->strip_center + 0.5 * p->strip_width);
+        d->heated_len = d->b - d->a;
+    } else {
+        d->heated_len = (double)h->ny;
+    }
+    const double ks[3] = {d->k0, d->k1, d->k2};
+    for (double k : ks)
+        if (!(k > 0.0 && k < 2.0))
+            return set_err(h, LBM_ERR_ARG, "g rates k0, k1, k2 must lie in (0, 2) (k0=%g k1=%g k2=%g)",
+                           d->k0, d->k1, d->k2);
+    if (p->flow_on) {
+        const double kf[3] = {d->k0f, d->k1f, d->k2f};
+        for (double k : kf)
+            if (!(k > 0.0 && k < 2.0))
+                return set_err(h, LBM_ERR_ARG, "flow rates must lie in (0, 2) (k0f=%g k1f=%g k2f=%g)",
+                               d->k0f, d->k1f, d->k2f);
+    }
+    if (!std::isfinite(p->init_amp)) return set_err(h, LBM_ERR_ARG, "init_amp must be finite");
+    return LBM_OK;
+}
+
+template <typename real>
+int enqueue_steps(lbm_s *h, long long n) {
+    for (long long k = 0; k < n; ++k) {
+        const bool last = (k == n - 1);
+        const long long next = h->step + 1;
+        const bool diag = last || (h->diag_every > 0 && next % h->diag_every == 0);
+        SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
+        a.step = next;
+        cudaError_t e = launch_lattice<real>(a, h->p.problem, h->p.flow_on != 0,
+                                             diag ? kSweepDiag : kSweep, h->grid, h->block,
+                                             h->stream);
+        if (e != cudaSuccess)
+            return set_err(h, LBM_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(e));
+        h->cur ^= 1;
+        h->has_prev = true;
+        h->step = next;
+    }
+    return LBM_OK;
+}
+
+template <typename real>
+int enqueue_init(lbm_s *h) {
+    SweepArgs<real> a = make_args<real>(h, nullptr, h->buf[h->cur]);
+    a.aux = static_cast<real *>(h->buf[h->cur ^ 1]);
+    a.step = 0;
+    cudaError_t e = launch_init<real>(a, h->p.init_amp, (uint64_t)h->p.seed, h->grid, h->block,
+                                      h->stream);
+    if (e != cudaSuccess)
+        return set_err(h, LBM_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+template <typename real>
+int enqueue_fields(lbm_s *h, double *out[6]) {
+    cudaError_t e;
+    if (h->step == 0 && !h->has_prev) {
+        SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], nullptr);
+        a.oH = out[0]; a.oT = out[1]; a.oFL = out[2]; a.oUX = out[3]; a.oUY = out[4]; a.oRHO = out[5];
+        e = launch_fields0<real>(a, h->p.flow_on != 0, h->grid, h->block, h->stream);
+    } else {
+        // Fields of step n are recomputed from the populations of step n-1,
+        // which the ping-pong buffer still holds.
+        SweepArgs<real> a = make_args<real>(h, h->buf[h->cur ^ 1], nullptr);
+        a.oH = out[0]; a.oT = out[1]; a.oFL = out[2]; a.oUX = out[3]; a.oUY = out[4]; a.oRHO = out[5];
+        e = launch_lattice<real>(a, h->p.problem, h->p.flow_on != 0, kFields, h->grid, h->block,
+                                 h->stream);
+    }
+    if (e != cudaSuccess)
+        return set_err(h, LBM_ERR_CUDA, "fields launch failed: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out) {
+    if (!out) return set_err(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 2 || ny < 2) return set_err(nullptr, LBM_ERR_ARG, "nx and ny must be >= 2");
+    if (ny > 65535 * kBlockY) return set_err(nullptr, LBM_ERR_ARG, "ny must be <= %d", 65535 * kBlockY);
+    if ((long long)nx * ny > (1ll << 31))
+        return set_err(nullptr, LBM_ERR_ARG, "lattice larger than 2^31 cells");
+    if (precision != LBM_FP32 && precision != LBM_FP64)
+        return set_err(nullptr, LBM_ERR_ARG, "precision must be LBM_FP32 or LBM_FP64");
+    lbm_s *h = new (std::nothrow) lbm_s();
+    if (!h) return set_err(nullptr, LBM_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return set_err(nullptr, LBM_ERR_CUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+    }
+    h->nx = nx;
+    h->ny = ny;
+    h->precision = precision;
+    h->esize = precision == LBM_FP64 ? 8 : 4;
+    const int row_align = (int)(128 / h->esize);        // 128 B rows
+    h->pitch = (nx + row_align - 1) / row_align * row_align;
+    const long long plane_align = 256 / (long long)h->esize;  // 256 B planes
+    h->pstride = ((long long)h->pitch * ny + plane_align - 1) / plane_align * plane_align;
+    h->block = dim3(kBlockX, kBlockY);
+    h->grid = dim3((nx + kBlockX - 1) / kBlockX, (ny + kBlockY - 1) / kBlockY);
+    h->alloc = g_alloc;
+    h->release = g_free;
+    h->alloc_ctx = g_alloc_ctx;
+    if (cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return set_err(nullptr, LBM_ERR_CUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+    }
+    // population buffers
+    for (int b = 0; b < 2; ++b) {
+        h->buf[b] = dev_alloc(h, buffer_bytes(h));
+        if (!h->buf[b]) {
+            lbm_destroy(h);
+            return set_err(nullptr, LBM_ERR_OOM, "device allocation of %zu bytes failed",
+                           buffer_bytes(h));
+        }
+    }
+    // reduction scratch: q partials, diag partials, 2 counters, record
+    const size_t nblk = (size_t)h->grid.x * h->grid.y;
+    const size_t nqmax = h->grid.x > h->grid.y ? h->grid.x : h->grid.y;
+    const size_t bytes = 256 + sizeof(DevRecord) + 256 + nqmax * 8 + nblk * 4 * 8 + 256;
+    h->scratch = dev_alloc(h, bytes);
+    if (!h->scratch) {
+        lbm_destroy(h);
+        return set_err(nullptr, LBM_ERR_OOM, "device allocation of scratch failed");
+    }
+    char *s = static_cast<char *>(h->scratch);
+    h->counters = reinterpret_cast<unsigned *>(s);
+    h->rec = reinterpret_cast<DevRecord *>(s + 256);
+    h->qpart = reinterpret_cast<double *>(s + 512);
+    h->dpart = reinterpret_cast<double *>(s + 512 + ((nqmax * 8 + 255) / 256) * 256);
+    e = cudaMemsetAsync(h->scratch, 0, bytes, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        lbm_destroy(h);
+        return set_err(nullptr, LBM_ERR_CUDA, "scratch clear failed: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_set_params(lbm_handle h, const lbm_params *p) {
+    if (!h || !p) return set_err(h, LBM_ERR_ARG, "NULL argument");
+    DeviceGuard g(h->device);
+    lbm_derived d;
+    int rc = derive(h, p, &d);
+    if (rc != LBM_OK) return rc;
+    h->p = *p;
+    h->d = d;
+    if (p->problem == LBM_CAVITY && p->strip_width > 0.0) {
+        // crossing abscissa x_c heated iff a <= x_c <= b; 2 x_c is an integer
+        h->lo2 = (int)std::ceil(2.0 * d.a);
+        h->hi2 = (int)std::floor(2.0 * d.b);
+        h->strip_on = 1;
+    } else {
+        h->lo2 = 0;
+        h->hi2 = -1;
+        h->strip_on = 0;
+    }
+    h->nq = p->problem == LBM_CAVITY ? (int)h->grid.x : (int)h->grid.y;
+    h->step = 0;
+    h->cur = 0;
+    h->has_prev = false;
+    CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned), h->stream));
+    rc = h->precision == LBM_FP64 ? enqueue_init<double>(h) : enqueue_init<float>(h);
+    if (rc != LBM_OK) return rc;
+    h->params_set = true;
+    return LBM_OK;
+}
+
+int lbm_get_derived(lbm_handle h, lbm_derived *out) {
+    if (!h || !out) return set_err(h, LBM_ERR_ARG, "NULL argument");
+    if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
+    *out = h->d;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, long long n) {
+    if (!h) return set_err(h, LBM_ERR_ARG, "NULL handle");
+    if (n < 0) return set_err(h, LBM_ERR_ARG, "n must be >= 0");
+    if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
+    if (n == 0) return LBM_OK;
+    DeviceGuard g(h->device);
+    return h->precision == LBM_FP64 ? enqueue_steps<double>(h, n) : enqueue_steps<float>(h, n);
+}
+
+int lbm_set_diag_every(lbm_handle h, long long k) {
+    if (!h || k < 0) return set_err(h, LBM_ERR_ARG, "bad argument");
+    h->diag_every = k;
+    return LBM_OK;
+}
+
+int lbm_read_fields(lbm_handle h, unsigned mask, double *H, double *T, double *fl, double *ux,
+                    double *uy, double *rho) {
+    if (!h) return set_err(h, LBM_ERR_ARG, "NULL handle");
+    if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
+    if (h->step > 0 && !h->has_prev)
+        return set_err(h, LBM_ERR_STATE, "no step taken since the populations were written");
+    DeviceGuard g(h->device);
+    const size_t P = (size_t)h->nx * h->ny;
+    if (!h->fields) {
+        h->fields = static_cast<double *>(dev_alloc(h, 6 * P * sizeof(double)));
+        if (!h->fields) return set_err(h, LBM_ERR_OOM, "device allocation of field staging failed");
+    }
+    double *host[6] = {H, T, fl, ux, uy, rho};
+    double *dev[6];
+    for (int k = 0; k < 6; ++k) dev[k] = ((mask >> k) & 1u) && host[k] ? h->fields + k * P : nullptr;
+    int rc = h->precision == LBM_FP64 ? enqueue_fields<double>(h, dev) : enqueue_fields<float>(h, dev);
+    if (rc != LBM_OK) return rc;
+    for (int k = 0; k < 6; ++k)
+        if (dev[k])
+            CUDA_TRY(h, cudaMemcpyAsync(host[k], dev[k], P * sizeof(double), cudaMemcpyDeviceToHost,
+                                        h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_handle h, lbm_diag *out) {
+    if (!h || !out) return set_err(h, LBM_ERR_ARG, "NULL argument");
+    if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
+    DeviceGuard g(h->device);
+    DevRecord r;
+    CUDA_TRY(h, cudaMemcpyAsync(&r, h->rec, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (r.valid != 1.0 || (long long)r.step != h->step)
+        return set_err(h, LBM_ERR_STATE, "no diagnostics for the current step");
+    const double P = (double)h->nx * (double)h->ny;
+    out->step = h->step;
+    out->melt_fraction = r.melt_sum / P;
+    out->H_total = r.H_sum;
+    out->Q_strip = r.Q_last;
+    out->Q_cum = r.Q_cum;
+    out->Nu = h->d.heated_len > 0.0 ? r.Q_last * h->d.Href / (h->d.alpha * h->d.heated_len) : 0.0;
+    out->front_x = r.melt_sum / (double)h->ny;
+    out->max_u = r.max_u;
+    out->nan_flag = r.nan_flag != 0.0 ? 1 : 0;
+    if (out->nan_flag) return set_err(h, LBM_ERR_DIVERGED, "non-finite H or rho at step %lld", h->step);
+    return LBM_OK;
+}
+
+int lbm_read_populations(lbm_handle h, double *f, double *g, long long *step) {
+    if (!h) return set_err(h, LBM_ERR_ARG, "NULL handle");
+    if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
+    DeviceGuard gd(h->device);
+    const size_t rowb = (size_t)h->nx * h->esize;
+    std::vector<char> stage((size_t)h->nx * h->ny * h->esize);
+    for (int pl = 0; pl < 18; ++pl) {
+        double *dst = pl < 9 ? f : g;
+        if (!dst) continue;
+        const char *src = static_cast<const char *>(h->buf[h->cur]) + (size_t)pl * h->pstride * h->esize;
+        CUDA_TRY(h, cudaMemcpy2DAsync(stage.data(), rowb, src, (size_t)h->pitch * h->esize, rowb, h->ny,
+                                      cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        double *o = dst + (size_t)(pl % 9) * h->nx * h->ny;
+        const size_t P = (size_t)h->nx * h->ny;
+        if (h->precision == LBM_FP64)
+            std::memcpy(o, stage.data(), P * sizeof(double));
+        else
+            for (size_t k = 0; k < P; ++k) o[k] = (double)reinterpret_cast<const float *>(stage.data())[k];
+    }
+    if (step) *step = h->step;
+    return LBM_OK;
+}
+
+int lbm_write_populations(lbm_handle h, const double *f, const double *g, long long step) {
+    if (!h || !f || !g || step < 0) return set_err(h, LBM_ERR_ARG, "bad argument");
+    if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
+    DeviceGuard gd(h->device);
+    const size_t P = (size_t)h->nx * h->ny;
+    const size_t rowb = (size_t)h->nx * h->esize;
+    std::vector<char> stage(P * h->esize);
+    for (int pl = 0; pl < 18; ++pl) {
+        const double *srcp = (pl < 9 ? f : g) + (size_t)(pl % 9) * P;
+        if (h->precision == LBM_FP64)
+            std::memcpy(stage.data(), srcp, P * sizeof(double));
+        else
+            for (size_t k = 0; k < P; ++k) reinterpret_cast<float *>(stage.data())[k] = (float)srcp[k];
+        // With the flow off the f planes are never rewritten by a sweep, so
+        // both buffers receive them.
+        const int nbuf = (pl < 9 && !h->p.flow_on) ? 2 : 1;
+        for (int b = 0; b < nbuf; ++b) {
+            char *dst = static_cast<char *>(h->buf[h->cur ^ b]) + (size_t)pl * h->pstride * h->esize;
+            CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, stage.data(), rowb, rowb,
+                                          h->ny, cudaMemcpyHostToDevice, h->stream));
+        }
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    }
+    h->step = step;
+    h->has_prev = false;
+    CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h) {
+    if (!h) return LBM_OK;
+    DeviceGuard g(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    dev_free(h, h->buf[0]);
+    dev_free(h, h->buf[1]);
+    dev_free(h, h->scratch);
+    dev_free(h, h->fields);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(lbm_handle h) { return h ? h->err : g_create_error; }
+
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *ctx) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return set_err(nullptr, LBM_ERR_ARG, "alloc and release must both be set or both NULL");
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_ctx = ctx;
+    return LBM_OK;
+}
+
+const char *lbm_version(void) { return "btrirt 0.1 sm_103a"; }
+
+}  // extern "C"

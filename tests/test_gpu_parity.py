@@ -1,0 +1,336 @@
+"""CUDA path vs the FP64 CPU oracle, through the C ABI.
+
+Bars: FP64 GPU path within 1e-12 of the oracle relative to each field's (or
+population plane set's) largest magnitude; FP32 path within 1e-5 max-abs in T
+and f_l after 1000 steps.  Sizes: the 64 x 32 cavity, ragged lattices that do
+not fill a 256-wide block, the 1024 x 4 Stefan problem, and sampled cells of
+the full 2048 x 1024 production cavity in the launch configuration the
+benchmark times.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1909_13086_gb300 import lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("H", "T", "fl", "ux", "uy", "rho")
+
+
+_STREAMS = []
+
+
+@pytest.fixture(scope="module")
+def stream():
+    """A dedicated CUDA stream lent to the library (kept alive for the module)."""
+    import torch
+
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    _STREAMS.append(s)
+    return s.cuda_stream
+
+
+def rel_err(got, want):
+    scale = np.abs(want).max()
+    return np.abs(got - want).max() / (scale if scale > 0 else 1.0)
+
+
+def assert_fields_fp64(got, want, tol=1e-12, names=FIELDS):
+    for k in names:
+        e = rel_err(got[k], want[k])
+        assert e <= tol, f"field {k}: relative error {e:.3e} > {tol:.1e}"
+
+
+def run_pair(orc, nx, ny, p, steps, prec, stream, threads=4):
+    ref = orc.Oracle(nx, ny, threads=threads, **p)
+    ref.step(steps)
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    lat.step(steps)
+    return ref, lat
+
+
+# ------------------------------------------------------------ FP64 parity
+def test_fp64_cavity_64x32_2000_steps(orc, stream):
+    nx, ny, p = workloads.cavity_64x32()
+    ref, lat = run_pair(orc, nx, ny, p, 2000, "fp64", stream)
+    assert_fields_fp64(lat.fields(), ref.fields())
+    f, g, step = lat.populations()
+    fr, gr = ref.populations()
+    assert step == 2000
+    assert rel_err(f, fr) <= 1e-12 and rel_err(g, gr) <= 1e-12
+    d, dr = lat.diagnostics(), ref.diagnostics()
+    for k in ("melt_fraction", "H_total", "Q_strip", "Q_cum", "Nu", "front_x", "max_u"):
+        assert d[k] == pytest.approx(dr[k], rel=1e-12, abs=1e-15), k
+    assert d["step"] == 2000 and d["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(67, 19, 400), (300, 37, 300), (2, 2, 50), (513, 3, 100)])
+def test_fp64_ragged_lattices(orc, stream, nx, ny, steps):
+    p = workloads.params(Ra=1e5, strip_center=0.45, strip_width=0.3)
+    ref, lat = run_pair(orc, nx, ny, p, steps, "fp64", stream)
+    assert_fields_fp64(lat.fields(), ref.fields())
+    d, dr = lat.diagnostics(), ref.diagnostics()
+    assert d["Q_cum"] == pytest.approx(dr["Q_cum"], rel=1e-12)
+    assert d["melt_fraction"] == pytest.approx(dr["melt_fraction"], rel=1e-12, abs=1e-16)
+
+
+def test_fp64_step_zero_and_every_step(orc, stream):
+    """Fields and diagnostics agree at step 0 and after each of the first steps."""
+    nx, ny, p = 48, 20, workloads.params(Ra=1e5)
+    ref = orc.Oracle(nx, ny, **p)
+    lat = lbm.Lattice(nx, ny, p, precision="fp64", stream=stream)
+    for n in range(6):
+        if n:
+            ref.step(1)
+            lat.step(1)
+        assert_fields_fp64(lat.fields(), ref.fields())
+        d, dr = lat.diagnostics(), ref.diagnostics()
+        assert d["step"] == n
+        for k in ("melt_fraction", "H_total", "Q_strip", "Q_cum"):
+            assert d[k] == pytest.approx(dr[k], rel=1e-12, abs=1e-15), (n, k)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("problem", ["cavity", "stefan"])
+def test_single_step_from_random_state(orc, stream, prec, tol, problem):
+    """Arbitrary non-equilibrium populations (solid, mushy and liquid cells,
+    every wall rule) advanced by one step on both sides."""
+    if problem == "cavity":
+        nx, ny, p = 70, 33, workloads.params(Ra=1e6, strip_center=0.4, strip_width=0.35)
+    else:
+        nx, ny, p = workloads.stefan_1024x4(Ste=0.5, alpha=0.1, k2=0.7, k0=1.2, nx=90)
+    f, g = workloads.random_populations(nx, ny, seed=11)
+    if prec == "fp32":  # both sides start from the same FP32-representable state
+        f, g = f.astype(np.float32).astype(np.float64), g.astype(np.float32).astype(np.float64)
+    ref = orc.Oracle(nx, ny, **p)
+    ref.set_populations(f, g, step=7)
+    ref.step(1)
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    lat.set_populations(f, g, step=7)
+    lat.step(1)
+    fo, go, step = lat.populations()
+    fr, gr = ref.populations()
+    assert step == 8
+    assert np.abs(go - gr).max() <= tol * max(1.0, np.abs(gr).max())
+    if p["flow_on"]:
+        assert np.abs(fo - fr).max() <= tol * max(1.0, np.abs(fr).max())
+    got, want = lat.fields(), ref.fields()
+    for k in FIELDS:
+        assert np.abs(got[k] - want[k]).max() <= tol * max(1.0, np.abs(want[k]).max()), k
+    assert lat.diagnostics()["Q_strip"] == pytest.approx(ref.diagnostics()["Q_strip"], rel=10 * tol,
+                                                         abs=10 * tol)
+
+
+# ------------------------------------------------------------ FP32 parity
+def test_fp32_cavity_1000_steps(orc, stream):
+    nx, ny, p = workloads.cavity_64x32()
+    ref, lat = run_pair(orc, nx, ny, p, 1000, "fp32", stream)
+    got, want = lat.fields(), ref.fields()
+    for k in ("T", "fl"):
+        e = np.abs(got[k] - want[k]).max()
+        assert e <= 1e-5, f"{k}: max-abs error {e:.3e}"
+    d, dr = lat.diagnostics(), ref.diagnostics()
+    assert d["melt_fraction"] == pytest.approx(dr["melt_fraction"], abs=1e-5)
+
+
+# ------------------------------------------------------------ Stefan
+def test_stefan_fp64_field_parity(orc, stream):
+    nx, ny, p = workloads.stefan_1024x4(Ste=1.0)
+    ref, lat = run_pair(orc, nx, ny, p, 10000, "fp64", stream, threads=8)
+    assert_fields_fp64(lat.fields(), ref.fields(), names=("H", "T", "fl"))
+    assert lat.diagnostics()["front_x"] == pytest.approx(ref.diagnostics()["front_x"], rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("Ste", [0.1, 1.0])
+def test_stefan_front_matches_neumann(orc, stream, prec, Ste):
+    """Front within one cell of X = 2 lambda sqrt(alpha t) from 1e3 steps on,
+    and within 1 % (2 % at Ste 0.1, where X(1e5) is only 57 cells) at 1e5."""
+    nx, ny, p = workloads.stefan_1024x4(Ste=Ste)
+    lam = orc.stefan_lambda(Ste)
+    alpha = p["alpha_override"]
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    done = 0
+    for n in (1000, 3000, 10000, 30000, 100000):
+        lat.step(n - done)
+        done = n
+        X = 2 * lam * math.sqrt(alpha * n)
+        xf = lat.diagnostics()["front_x"]
+        assert abs(xf - X) <= 1.0, (n, xf, X)
+    assert xf == pytest.approx(X, rel=0.02 if Ste < 0.5 else 0.01)
+    T = lat.fields(("T",))["T"][0]
+    x = np.arange(nx) + 0.5
+    liquid = x < X - 1.0
+    Tn = np.array([orc.neumann_T(xx, done, alpha, lam) for xx in x[liquid]])
+    assert np.abs(T[liquid] - Tn).max() <= 1e-2
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("fp32", 1e-6)])
+def test_one_cell_interface_on_gpu(stream, prec, tol):
+    """Eq. 6: with k1 + k2 = 2 the solid ahead of the front stays at H_s and
+    the interface is one cell wide (checked every 50 steps)."""
+    alpha = (1.0 / 1.5 - 0.5) / 3.0  # k1 = 1.5 through Eq. 5
+    nx, ny, p = workloads.stefan_1024x4(Ste=0.1, alpha=alpha, k2=0.5, nx=256)
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    eps = 1e-12 if prec == "fp64" else 1e-5
+    for _ in range(40):
+        lat.step(50)
+        F = lat.fields(("H", "fl"))
+        fl, H = F["fl"], F["H"]
+        assert ((fl > eps) & (fl < 1 - eps)).sum(axis=1).max() <= 1
+        for row in range(ny):
+            melted = np.nonzero(fl[row] > eps)[0]
+            edge = melted.max() if melted.size else -1
+            assert np.abs(H[row, edge + 1:]).max(initial=0.0) <= tol
+
+
+# ------------------------------------------------------------ invariants
+def test_mirror_symmetry_gpu(stream):
+    nx, ny = 128, 64
+    p = workloads.params(Ra=1e5, init_amp=0.0)
+    lat = lbm.Lattice(nx, ny, p, precision="fp64", stream=stream)
+    lat.step(1500)
+    F = lat.fields()
+    assert F["fl"].max() > 0
+    for k in ("H", "T", "fl", "uy", "rho"):
+        a = F[k]
+        assert np.abs(a - a[:, ::-1]).max() <= max(1e-12 * np.abs(a).max(), 1e-14), k
+    assert np.abs(F["ux"] + F["ux"][:, ::-1]).max() <= max(1e-12 * np.abs(F["ux"]).max(), 1e-14)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_energy_budget_gpu(stream, prec):
+    nx, ny, p = workloads.cavity_64x32()
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    h0 = lat.diagnostics()["H_total"]
+    lat.step(3000)
+    d = lat.diagnostics()
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    assert abs(d["H_total"] - h0 - d["Q_cum"]) <= tol * d["Q_cum"]
+
+
+def test_checkpoint_resume_is_bitwise(stream):
+    nx, ny, p = 96, 40, workloads.params(Ra=1e5)
+    for prec in ("fp64", "fp32"):
+        a = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+        a.step(400)
+        fa, ga, _ = a.populations()
+        b = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+        b.step(200)
+        f, g, step = b.populations()
+        c = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+        c.set_populations(f, g, step)
+        c.step(200)
+        fc, gc, stepc = c.populations()
+        assert stepc == 400
+        assert np.array_equal(fa, fc) and np.array_equal(ga, gc)
+
+
+def test_deterministic_diagnostics(stream):
+    nx, ny, p = 700, 300, workloads.params(Ra=1e6)
+    runs = []
+    for _ in range(2):
+        lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+        lat.step(100)
+        runs.append(lat.diagnostics())
+    assert runs[0] == runs[1]
+
+
+# ------------------------------------------------------------ errors
+def test_errors_and_edge_cases(stream):
+    nx, ny, p = workloads.cavity_64x32()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(1, 8, p, stream=stream)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(nx, ny, dict(p, k0=2.5), stream=stream)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice(nx, ny, dict(p, Ste=0.0), stream=stream)
+    lat = lbm.Lattice(nx, ny, p, stream=stream)
+    lat.step(0)
+    assert lat.diagnostics()["step"] == 0
+    with pytest.raises(lbm.LbmError):
+        lat.step(-1)
+    f, g, _ = lat.populations()
+    lat.set_populations(f, g, 5)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.fields()
+    assert e.value.status == lbm.LBM_ERR_STATE
+    with pytest.raises(lbm.LbmError) as e:
+        lat.diagnostics()
+    assert e.value.status == lbm.LBM_ERR_STATE
+    # a non-finite state is reported, not hidden
+    g = g.copy()
+    g[0, 3, 4] = np.nan
+    lat.set_populations(f, g, 0)
+    lat.step(1)
+    d = lat.diagnostics(raise_on_diverged=False)
+    assert d["nan_flag"] == 1
+    with pytest.raises(lbm.LbmError) as e:
+        lat.diagnostics()
+    assert e.value.status == lbm.LBM_ERR_DIVERGED
+
+
+def test_torch_allocator_hook(orc, stream):
+    import torch
+
+    lbm.use_torch_allocator()
+    try:
+        before = torch.cuda.memory_allocated()
+        nx, ny, p = workloads.cavity_64x32()
+        lat = lbm.Lattice(nx, ny, p, precision="fp64", stream=stream)
+        assert torch.cuda.memory_allocated() > before
+        lat.step(100)
+        ref = orc.Oracle(nx, ny, **p)
+        ref.step(100)
+        assert_fields_fp64(lat.fields(), ref.fields())
+        lat.close()
+        assert torch.cuda.memory_allocated() == before
+    finally:
+        lbm.lib().lbm_set_allocator(lbm.ALLOC_FN(), lbm.FREE_FN(), None)
+
+
+# ------------------------------------------------------------ full size
+def test_full_size_sampled_parity_fp32(orc, stream):
+    """2048 x 1024 production cavity, FP32, the benchmark's launch shape: one
+    step from the GPU's own step-(n-1) populations recomputed by the oracle on
+    sampled cells (every boundary row and column, the strip edges, random
+    interior cells)."""
+    nx, ny, p = workloads.cavity_2048x1024()
+    lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    lat.step(30)
+    fprev, gprev, _ = lat.populations()
+    lat.step(1)
+    fnew, gnew, _ = lat.populations()
+    F = lat.fields()
+    ref = orc.Oracle(nx, ny, **p)
+    rng = np.random.default_rng(5)
+    d = ref.derived()
+    cells = [(x, y) for x in (0, 1, nx - 2, nx - 1) for y in range(0, ny, 97)]
+    cells += [(x, y) for y in (0, 1, ny - 2, ny - 1) for x in range(0, nx, 61)]
+    for xs in (int(math.floor(d["a"])) + k for k in (-2, -1, 0, 1)):
+        cells += [(xs, 0), (xs, 1), (nx - 1 - xs, 0)]
+    cells += [(int(x), int(y)) for x, y in zip(rng.integers(0, nx, 400), rng.integers(0, ny, 400))]
+    for x, y in cells:
+        fo, go, m, _ = ref.cell_update(fprev, gprev, x, y)
+        assert np.abs(go - gnew[:, y, x]).max() <= 1e-5, (x, y)
+        assert np.abs(fo - fnew[:, y, x]).max() <= 1e-5, (x, y)
+        for k, name in enumerate(FIELDS):
+            assert abs(m[k] - F[name][y, x]) <= 1e-5, (x, y, name)
+
+
+def test_full_size_budget_and_bounds_fp32(stream):
+    nx, ny, p = workloads.cavity_2048x1024()
+    lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    d0 = lat.diagnostics()
+    lat.step(2000)
+    d = lat.diagnostics()
+    assert d["nan_flag"] == 0 and d["Q_cum"] > 0
+    assert 0.0 <= d["melt_fraction"] <= 1.0 and d["melt_fraction"] > d0["melt_fraction"]
+    assert abs(d["H_total"] - d0["H_total"] - d["Q_cum"]) <= 1e-3 * d["Q_cum"]
+    assert d["max_u"] < 0.3
