@@ -135,6 +135,11 @@ int lbm_step(lbm_handle h, long long n);
  * each lbm_step call only, the default). */
 int lbm_set_diag_every(lbm_handle h, long long k);
 
+/* Launch shape: rows of the lattice walked by each thread of a block (1 to
+ * 1024, default 4).  Results do not depend on it except for the rounding of
+ * the FP32 in-warp diagnostic partial sums.  Used by the tuner. */
+int lbm_set_rows_per_block(lbm_handle h, int rows);
+
 /* Bit mask selecting the fields of lbm_read_fields. */
 enum { LBM_FIELD_H = 1, LBM_FIELD_T = 2, LBM_FIELD_FL = 4, LBM_FIELD_UX = 8,
        LBM_FIELD_UY = 16, LBM_FIELD_RHO = 32, LBM_FIELD_ALL = 63 };

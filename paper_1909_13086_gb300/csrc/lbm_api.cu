@@ -27,16 +27,15 @@ lbm_alloc_fn g_alloc = nullptr;
 lbm_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
 
-constexpr int kBlockX = 256;  // threads along x per block (8 warps)
-constexpr int kBlockY = 1;
+constexpr int kDefaultRows = 4;  // rows walked by each thread of a block
 
 }  // namespace
 
 struct lbm_s {
     int nx = 0, ny = 0, precision = LBM_FP32, device = 0;
     size_t esize = 4;           // bytes per population value
-    int pitch = 0;              // row pitch, elements
-    long long pstride = 0;      // plane stride, elements
+    int ntx = 0;                // column tiles of kTW cells
+    int rows = kDefaultRows;    // rows per block
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *buf[2] = {nullptr, nullptr};  // 18 planes each
@@ -55,8 +54,9 @@ struct lbm_s {
     unsigned *counters = nullptr;
     DevRecord *rec = nullptr;
     int nq = 0;
-    // field output staging (6 x nx*ny doubles), allocated on first use
-    double *fields = nullptr;
+    // FP64 staging for field and population read-back / write (18 x nx*ny
+    // doubles), allocated on first use
+    double *stage = nullptr;
     // allocator used for this handle's memory
     lbm_alloc_fn alloc = nullptr;
     lbm_free_fn release = nullptr;
@@ -112,7 +112,20 @@ void dev_free(lbm_s *h, void *p) {
         cudaFree(p);
 }
 
-size_t buffer_bytes(const lbm_s *h) { return (size_t)18 * (size_t)h->pstride * h->esize; }
+size_t buffer_bytes(const lbm_s *h) {
+    return (size_t)h->ntx * (size_t)h->ny * (size_t)kRS * h->esize;
+}
+
+void set_grid(lbm_s *h) {
+    h->block = dim3(kTW);
+    h->grid = dim3(h->ntx, (h->ny + h->rows - 1) / h->rows);
+}
+
+double *staging(lbm_s *h) {
+    if (!h->stage)
+        h->stage = static_cast<double *>(dev_alloc(h, (size_t)kPlanes * h->nx * h->ny * sizeof(double)));
+    return h->stage;
+}
 
 template <typename real>
 SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
@@ -121,8 +134,8 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.dst = static_cast<real *>(dst);
     a.nx = h->nx;
     a.ny = h->ny;
-    a.pitch = h->pitch;
-    a.pstride = h->pstride;
+    a.ntx = h->ntx;
+    a.rows = h->rows;
     a.k0 = (real)h->d.k0;
     a.k1 = (real)h->d.k1;
     a.k2 = (real)h->d.k2;
@@ -250,6 +263,14 @@ int enqueue_fields(lbm_s *h, double *out[6]) {
     return LBM_OK;
 }
 
+template <typename real>
+int repack(lbm_s *h, void *buf, void *buf2, bool to_staging) {
+    cudaError_t e = launch_repack<real>(static_cast<real *>(buf), static_cast<real *>(buf2), h->stage,
+                                       h->nx, h->ny, to_staging, h->stream);
+    if (e != cudaSuccess) return set_err(h, LBM_ERR_CUDA, "repack launch failed: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -258,7 +279,7 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     if (!out) return set_err(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (nx < 2 || ny < 2) return set_err(nullptr, LBM_ERR_ARG, "nx and ny must be >= 2");
-    if (ny > 65535 * kBlockY) return set_err(nullptr, LBM_ERR_ARG, "ny must be <= %d", 65535 * kBlockY);
+    if (ny > 65535) return set_err(nullptr, LBM_ERR_ARG, "ny must be <= 65535");
     if ((long long)nx * ny > (1ll << 31))
         return set_err(nullptr, LBM_ERR_ARG, "lattice larger than 2^31 cells");
     if (precision != LBM_FP32 && precision != LBM_FP64)
@@ -274,12 +295,8 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     h->ny = ny;
     h->precision = precision;
     h->esize = precision == LBM_FP64 ? 8 : 4;
-    const int row_align = (int)(128 / h->esize);        // 128 B rows
-    h->pitch = (nx + row_align - 1) / row_align * row_align;
-    const long long plane_align = 256 / (long long)h->esize;  // 256 B planes
-    h->pstride = ((long long)h->pitch * ny + plane_align - 1) / plane_align * plane_align;
-    h->block = dim3(kBlockX, kBlockY);
-    h->grid = dim3((nx + kBlockX - 1) / kBlockX, (ny + kBlockY - 1) / kBlockY);
+    h->ntx = (nx + kTW - 1) / kTW;
+    set_grid(h);
     h->alloc = g_alloc;
     h->release = g_free;
     h->alloc_ctx = g_alloc_ctx;
@@ -303,8 +320,9 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
         }
     }
     // reduction scratch: q partials, diag partials, 2 counters, record
-    const size_t nblk = (size_t)h->grid.x * h->grid.y;
-    const size_t nqmax = h->grid.x > h->grid.y ? h->grid.x : h->grid.y;
+    // sized for the largest grid any rows-per-block setting can produce (1 row)
+    const size_t nblk = (size_t)h->ntx * (size_t)ny;
+    const size_t nqmax = (size_t)(h->ntx > ny ? h->ntx : ny);
     const size_t bytes = 256 + sizeof(DevRecord) + 256 + nqmax * 8 + nblk * 4 * 8 + 256;
     h->scratch = dev_alloc(h, bytes);
     if (!h->scratch) {
@@ -386,13 +404,11 @@ int lbm_read_fields(lbm_handle h, unsigned mask, double *H, double *T, double *f
         return set_err(h, LBM_ERR_STATE, "no step taken since the populations were written");
     DeviceGuard g(h->device);
     const size_t P = (size_t)h->nx * h->ny;
-    if (!h->fields) {
-        h->fields = static_cast<double *>(dev_alloc(h, 6 * P * sizeof(double)));
-        if (!h->fields) return set_err(h, LBM_ERR_OOM, "device allocation of field staging failed");
-    }
+    double *stage = staging(h);
+    if (!stage) return set_err(h, LBM_ERR_OOM, "device allocation of the read-back staging failed");
     double *host[6] = {H, T, fl, ux, uy, rho};
     double *dev[6];
-    for (int k = 0; k < 6; ++k) dev[k] = ((mask >> k) & 1u) && host[k] ? h->fields + k * P : nullptr;
+    for (int k = 0; k < 6; ++k) dev[k] = ((mask >> k) & 1u) && host[k] ? stage + k * P : nullptr;
     int rc = h->precision == LBM_FP64 ? enqueue_fields<double>(h, dev) : enqueue_fields<float>(h, dev);
     if (rc != LBM_OK) return rc;
     for (int k = 0; k < 6; ++k)
@@ -430,22 +446,17 @@ int lbm_read_populations(lbm_handle h, double *f, double *g, long long *step) {
     if (!h) return set_err(h, LBM_ERR_ARG, "NULL handle");
     if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
     DeviceGuard gd(h->device);
-    const size_t rowb = (size_t)h->nx * h->esize;
-    std::vector<char> stage((size_t)h->nx * h->ny * h->esize);
-    for (int pl = 0; pl < 18; ++pl) {
-        double *dst = pl < 9 ? f : g;
-        if (!dst) continue;
-        const char *src = static_cast<const char *>(h->buf[h->cur]) + (size_t)pl * h->pstride * h->esize;
-        CUDA_TRY(h, cudaMemcpy2DAsync(stage.data(), rowb, src, (size_t)h->pitch * h->esize, rowb, h->ny,
-                                      cudaMemcpyDeviceToHost, h->stream));
-        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-        double *o = dst + (size_t)(pl % 9) * h->nx * h->ny;
-        const size_t P = (size_t)h->nx * h->ny;
-        if (h->precision == LBM_FP64)
-            std::memcpy(o, stage.data(), P * sizeof(double));
-        else
-            for (size_t k = 0; k < P; ++k) o[k] = (double)reinterpret_cast<const float *>(stage.data())[k];
-    }
+    if (!staging(h)) return set_err(h, LBM_ERR_OOM, "device allocation of the staging failed");
+    const size_t half = (size_t)9 * h->nx * h->ny;
+    int rc = h->precision == LBM_FP64 ? repack<double>(h, h->buf[h->cur], nullptr, true)
+                                      : repack<float>(h, h->buf[h->cur], nullptr, true);
+    if (rc != LBM_OK) return rc;
+    if (f)
+        CUDA_TRY(h, cudaMemcpyAsync(f, h->stage, half * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (g)
+        CUDA_TRY(h, cudaMemcpyAsync(g, h->stage + half, half * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (step) *step = h->step;
     return LBM_OK;
 }
@@ -454,29 +465,28 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
     if (!h || !f || !g || step < 0) return set_err(h, LBM_ERR_ARG, "bad argument");
     if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
     DeviceGuard gd(h->device);
-    const size_t P = (size_t)h->nx * h->ny;
-    const size_t rowb = (size_t)h->nx * h->esize;
-    std::vector<char> stage(P * h->esize);
-    for (int pl = 0; pl < 18; ++pl) {
-        const double *srcp = (pl < 9 ? f : g) + (size_t)(pl % 9) * P;
-        if (h->precision == LBM_FP64)
-            std::memcpy(stage.data(), srcp, P * sizeof(double));
-        else
-            for (size_t k = 0; k < P; ++k) reinterpret_cast<float *>(stage.data())[k] = (float)srcp[k];
-        // With the flow off the f planes are never rewritten by a sweep, so
-        // both buffers receive them.
-        const int nbuf = (pl < 9 && !h->p.flow_on) ? 2 : 1;
-        for (int b = 0; b < nbuf; ++b) {
-            char *dst = static_cast<char *>(h->buf[h->cur ^ b]) + (size_t)pl * h->pstride * h->esize;
-            CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, stage.data(), rowb, rowb,
-                                          h->ny, cudaMemcpyHostToDevice, h->stream));
-        }
-        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    }
+    if (!staging(h)) return set_err(h, LBM_ERR_OOM, "device allocation of the staging failed");
+    const size_t half = (size_t)9 * h->nx * h->ny;
+    CUDA_TRY(h, cudaMemcpyAsync(h->stage, f, half * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->stage + half, g, half * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
+    // With the flow off the f planes are never rewritten by a sweep, so both
+    // buffers receive them.
+    void *other = h->p.flow_on ? nullptr : h->buf[h->cur ^ 1];
+    int rc = h->precision == LBM_FP64 ? repack<double>(h, h->buf[h->cur], other, false)
+                                      : repack<float>(h, h->buf[h->cur], other, false);
+    if (rc != LBM_OK) return rc;
     h->step = step;
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_rows_per_block(lbm_handle h, int rows) {
+    if (!h || rows < 1 || rows > 1024) return set_err(h, LBM_ERR_ARG, "rows must be in [1, 1024]");
+    h->rows = rows;
+    set_grid(h);
     return LBM_OK;
 }
 
@@ -487,7 +497,7 @@ int lbm_destroy(lbm_handle h) {
     dev_free(h, h->buf[0]);
     dev_free(h, h->buf[1]);
     dev_free(h, h->scratch);
-    dev_free(h, h->fields);
+    dev_free(h, h->stage);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return LBM_OK;

@@ -12,9 +12,24 @@ enum Problem { kCavity = 0, kStefan = 1 };
 // What one launch of the lattice kernel does.
 enum Mode {
     kSweep = 0,      // stream + collide, write the next populations
-    kSweepDiag = 1,  // same, plus the fused FP64 diagnostics reductions
+    kSweepDiag = 1,  // same, plus the fused diagnostics reductions
     kFields = 2,     // stream + macroscopic step only: write the fields, no populations
 };
+
+// Population layout in device memory ("tile-major structure of arrays").
+// The lattice is cut into column tiles of kTW cells.  Within a tile, each row
+// holds the 18 planes (f_0..f_8, g_0..g_8) one after the other, kTW values
+// each, and rows follow one another:
+//     index(x, y, p) = ((x / kTW) * ny + y) * 18 * kTW + p * kTW + x % kTW.
+// A warp's 18 loads of one cell row are then one base register plus
+// compile-time offsets (plane p: p*kTW; row above / below: -/+ 18*kTW).
+constexpr int kTW = 256;
+constexpr int kPlanes = 18;
+constexpr int kRS = kPlanes * kTW;  // elements per tile row
+
+__host__ __device__ inline long long pop_index(int x, int y, int p, int ny) {
+    return ((long long)(x / kTW) * ny + y) * kRS + (long long)p * kTW + (x % kTW);
+}
 
 // FP64 diagnostics record living in device memory (one per handle).
 struct DevRecord {
@@ -31,13 +46,13 @@ struct DevRecord {
 // Arguments of every lattice kernel, passed by value.
 template <typename real>
 struct SweepArgs {
-    const real *src;       // 18 planes: f_0..f_8 then g_0..g_8
-    real *dst;             // same layout (sweep modes)
+    const real *src;       // tile-major populations of the previous step
+    real *dst;             // tile-major populations written by this step
     real *aux;             // init only: the other buffer, whose f planes are also
                            // set to w_i (they are never rewritten when flow is off)
     int nx, ny;            // lattice size
-    int pitch;             // row pitch, elements
-    long long pstride;     // plane stride, elements
+    int ntx;               // number of column tiles
+    int rows;              // rows per block (each thread walks them)
     real k0, k1, k2;       // g rates (Eq. 2)
     real k0f, k1f, k2f;    // f rates
     real Lh, gbeta;        // latent heat, g*beta
@@ -66,5 +81,11 @@ cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim
 template <typename real>
 cudaError_t launch_fields0(const SweepArgs<real> &a, bool flow, dim3 grid, dim3 block,
                            cudaStream_t s);
+// Tile-major buffer <-> plane-major FP64 staging (18 planes of nx*ny, f then g).
+// to_staging = true packs buf into stage; false unpacks stage into buf (and,
+// if buf2 is non-NULL, the f planes into buf2 as well).
+template <typename real>
+cudaError_t launch_repack(real *buf, real *buf2, double *stage, int nx, int ny, bool to_staging,
+                          cudaStream_t s);
 
 }  // namespace btrirt

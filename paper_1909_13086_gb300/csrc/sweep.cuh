@@ -1,10 +1,11 @@
 // sweep.cuh -- the fused B-TriRT collide-and-stream kernel (device code).
 //
-// One thread per lattice cell.  Populations are structure-of-arrays planes
-// (f_0..f_8, g_0..g_8), rows padded to 128 B.  The pull scheme reads each
-// post-collision population of the previous step exactly once, so the only
-// DRAM traffic is 18 loads + 18 stores per cell; the +-1 x-offset planes cost
-// one extra 32 B sector per warp, which L1/L2 absorb.
+// Layout: tile-major structure of arrays (lbm_internal.h).  One thread per
+// lattice column of a kTW-wide tile, walking `rows` rows; a warp covers 32
+// consecutive cells of one row, so every load and store is a coalesced 128 B
+// line (FP32).  In the interior the 18 pull loads of a cell are one base
+// register plus compile-time offsets; boundary rows and the two warps of a
+// row that touch a side wall take a generic path with the wall rules.
 //
 // Per cell, in one pass (paper Sec. 2 and the readings of Sec. 3):
 //   1. pull streaming; half-way bounce-back on no-slip / adiabatic walls,
@@ -16,7 +17,15 @@
 //   5. f collision: the same block operator with rates (k0f, k1f, k2f) and a
 //      forcing term whose first and second moments are (1 - k1f/2) F and
 //      (1 - k2f/2)(uF + Fu);
-//   6. store; optionally reduce the diagnostics in FP64.
+//   6. store; reduce the heated-wall inflow (and the diagnostics).
+//
+// The collisions are evaluated in moment space.  With a = 1 - k0, Eq. 2 reads
+//   p*_i = a p_i + k0 p^eq_i - w_i [3 c_i.A1 + 9/2 Q_i:A2],  Q_i = c_i c_i - I/3,
+// where A1 = (k1 - k0) M1 and A2 = (k2 - k0) M2 are built from the raw moments
+// of p minus the equilibrium moments (Eq. 4: sum c g_eq = T u, sum cc g_eq =
+// T/3 I; flow: rho u and rho (I/3 + uu)).  Folding p^eq in gives
+//   p*_i = a p_i + w_i [B0 + 3 c_i.B1 + 9/2 Q_i:B2]  (+ k0 (H - T) for g_0),
+// about 4 flops per population instead of re-forming every n_i.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,8 +36,7 @@
 
 namespace btrirt {
 
-// ---- D2Q9 (c_i, w_i, opposite) as constexpr functions: fully folded once the
-//      direction loops are unrolled.
+// ---- D2Q9 (c_i, w_i, opposite), folded at compile time in unrolled loops.
 __host__ __device__ constexpr int cx_of(int i) {
     return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
 }
@@ -43,62 +51,208 @@ __device__ __forceinline__ real w_of(int i) {
     return i == 0 ? real(4) / real(9) : (i <= 4 ? real(1) / real(9) : real(1) / real(36));
 }
 
-// Q_i : A with Q_i = c_i c_i - I/3 and A symmetric (xx, xy, yy).
+// ---- H -> (T, f_l): H_s = C_p T_m = 0, H_l = H_s + L.
 template <typename real>
-__device__ __forceinline__ real q_dot(int i, real axx, real axy, real ayy) {
-    const real third = real(1) / real(3);
-    const int cx = cx_of(i), cy = cy_of(i);
-    return (real(cx * cx) - third) * axx + real(2 * cx * cy) * axy +
-           (real(cy * cy) - third) * ayy;
-}
-
-// Moments of a D2Q9 vector n: M1 = sum c n, M2 = sum c c n.
-template <typename real>
-__device__ __forceinline__ void moments(const real n[9], real &m1x, real &m1y, real &m2xx,
-                                        real &m2xy, real &m2yy) {
-    m1x = (n[1] - n[3]) + (n[5] - n[6]) + (n[8] - n[7]);
-    m1y = (n[2] - n[4]) + (n[5] + n[6]) - (n[7] + n[8]);
-    const real diag = (n[5] + n[6]) + (n[7] + n[8]);
-    m2xx = (n[1] + n[3]) + diag;
-    m2yy = (n[2] + n[4]) + diag;
-    m2xy = (n[5] + n[7]) - (n[6] + n[8]);
-}
-
-// out_i = p_i - k0 n_i - w_i [ 3 c_i.A1 + 9/2 Q_i:A2 ]  (Eq. 2 with
-// A1 = (k1 - k0) M1 - source_1 and A2 = (k2 - k0) M2 - source_2 folded in).
-template <typename real>
-__device__ __forceinline__ void block_relax(real p[9], const real n[9], real k0, real a1x,
-                                            real a1y, real a2xx, real a2xy, real a2yy) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const real c1 = real(cx_of(i)) * a1x + real(cy_of(i)) * a1y;
-        p[i] = p[i] - k0 * n[i] -
-               w_of<real>(i) * (real(3) * c1 + real(4.5) * q_dot<real>(i, a2xx, a2xy, a2yy));
+__device__ __forceinline__ void invert(real H, real Lh, real &T, real &fl) {
+    if (H <= real(0)) {
+        T = H;
+        fl = real(0);
+    } else if (H >= Lh) {
+        T = H - Lh;
+        fl = real(1);
+    } else {
+        T = real(0);
+        fl = H / Lh;
     }
 }
 
-// ---- block reductions (deterministic for a fixed block shape) ----
-__device__ __forceinline__ double warp_sum(double v) {
+// p_i <- a p_i + w_i [B0 + 3 c_i.B1 + 9/2 Q_i:B2]  for all nine directions.
+template <typename real>
+__device__ __forceinline__ void emit(real p[9], real a, real B0, real B1x, real B1y, real B2xx,
+                                     real B2xy, real B2yy) {
+    const real third = real(1) / real(3);
+    const real w0 = real(4) / real(9), w1 = real(1) / real(9), w5 = real(1) / real(36);
+    const real q0 = -(B2xx + B2yy) * third;
+    const real q13 = (real(2) * B2xx - B2yy) * third;
+    const real q24 = (real(2) * B2yy - B2xx) * third;
+    const real s = real(2) * third * (B2xx + B2yy);
+    const real q57 = s + real(2) * B2xy;
+    const real q68 = s - real(2) * B2xy;
+    p[0] = a * p[0] + w0 * (B0 + real(4.5) * q0);
+    const real e13 = w1 * (B0 + real(4.5) * q13), t1 = real(3) * w1 * B1x;
+    p[1] = a * p[1] + (e13 + t1);
+    p[3] = a * p[3] + (e13 - t1);
+    const real e24 = w1 * (B0 + real(4.5) * q24), t2 = real(3) * w1 * B1y;
+    p[2] = a * p[2] + (e24 + t2);
+    p[4] = a * p[4] + (e24 - t2);
+    const real e57 = w5 * (B0 + real(4.5) * q57), t5 = real(3) * w5 * (B1x + B1y);
+    p[5] = a * p[5] + (e57 + t5);
+    p[7] = a * p[7] + (e57 - t5);
+    const real e68 = w5 * (B0 + real(4.5) * q68), t6 = real(3) * w5 * (B1y - B1x);
+    p[6] = a * p[6] + (e68 + t6);
+    p[8] = a * p[8] + (e68 - t6);
+}
+
+// Raw first and second moments of nine populations.
+template <typename real>
+__device__ __forceinline__ void raw_moments(const real p[9], real &jx, real &jy, real &pxx,
+                                            real &pxy, real &pyy) {
+    jx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
+    jy = (p[2] - p[4]) + (p[5] + p[6]) - (p[7] + p[8]);
+    const real d = (p[5] + p[6]) + (p[7] + p[8]);
+    pxx = (p[1] + p[3]) + d;
+    pyy = (p[2] + p[4]) + d;
+    pxy = (p[5] + p[7]) - (p[6] + p[8]);
+}
+
+template <typename real>
+__device__ __forceinline__ real sum9(const real p[9]) {
+    return (((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]))) + p[8];
+}
+
+template <typename real>
+struct Macro {
+    real H, T, fl, rho, ux, uy;
+};
+
+// Steps 2-5 on one cell: macroscopic fields, then both collisions in place
+// (COLLIDE = false stops after the fields).
+template <typename real, bool FLOW, bool COLLIDE>
+__device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, real f[9], real g[9]) {
+    Macro<real> m;
+    real jx = real(0), jy = real(0);
+    m.rho = real(1);
+    if (FLOW) {
+        m.rho = sum9(f);
+        jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    }
+    m.H = sum9(g);
+    invert(m.H, a.Lh, m.T, m.fl);
+    real Fy = real(0);
+    m.ux = real(0);
+    m.uy = real(0);
+    if (FLOW) {
+        Fy = a.gbeta * m.T;
+        const real inv_rho = real(1) / m.rho;
+        m.ux = m.fl * jx * inv_rho;
+        m.uy = m.fl * (jy + real(0.5) * Fy) * inv_rho;
+    }
+    if (!COLLIDE) return m;
+
+    const real third = real(1) / real(3);
+    // ---- g (Eq. 2 with Eq. 4)
+    {
+        real gjx, gjy, gxx, gxy, gyy;
+        raw_moments(g, gjx, gjy, gxx, gxy, gyy);
+        const real T = m.T, T3 = m.T * third;
+        const real d1 = a.k1 - a.k0, d2 = a.k2 - a.k0;
+        const real k0T = a.k0 * T;
+        const real B1x = k0T * m.ux - d1 * (gjx - T * m.ux);
+        const real B1y = k0T * m.uy - d1 * (gjy - T * m.uy);
+        const real H = m.H;
+        emit(g, real(1) - a.k0, k0T, B1x, B1y, -d2 * (gxx - T3), -d2 * gxy, -d2 * (gyy - T3));
+        g[0] += a.k0 * (H - T);
+    }
+    // ---- f (same block operator, forcing folded into A1 and A2)
+    if (FLOW) {
+        real fjx, fjy, fxx, fxy, fyy;
+        raw_moments(f, fjx, fjy, fxx, fxy, fyy);
+        const real rho = m.rho, ux = m.ux, uy = m.uy;
+        const real rux = rho * ux, ruy = rho * uy;
+        const real rxx = rux * ux, rxy = rux * uy, ryy = ruy * uy, r3 = rho * third;
+        const real d1 = a.k1f - a.k0f, d2 = a.k2f - a.k0f;
+        const real s1 = real(1) - real(0.5) * a.k1f, s2 = real(1) - real(0.5) * a.k2f;
+        const real A1x = d1 * (fjx - rux);
+        const real A1y = d1 * (fjy - ruy) - s1 * Fy;
+        const real A2xx = d2 * (fxx - r3 - rxx);
+        const real A2xy = d2 * (fxy - rxy) - s2 * ux * Fy;
+        const real A2yy = d2 * (fyy - r3 - ryy) - s2 * real(2) * uy * Fy;
+        const real k0 = a.k0f;
+        emit(f, real(1) - k0, k0 * rho, k0 * rux - A1x, k0 * ruy - A1y, k0 * rxx - A2xx,
+             k0 * rxy - A2xy, k0 * ryy - A2yy);
+    }
+    return m;
+}
+
+// ---- streaming ----
+// Interior cell: no wall in reach.  b points at (x, y, plane 0); bL / bR equal
+// b except at the tile's first / last column, where they are shifted so that
+// bL[-1] / bR[+1] land in the neighbouring tile.
+template <typename real, bool FLOW>
+__device__ __forceinline__ void pull_fast(const real *__restrict__ b, const real *__restrict__ bL,
+                                          const real *__restrict__ bR, real f[9], real g[9]) {
+    constexpr int R = kRS, W = kTW;
+#define BTRIRT_PULL(P, arr)                                          \
+    arr[0] = __ldg(b + (P + 0) * W);                                 \
+    arr[1] = __ldg(bL + (P + 1) * W - 1);                            \
+    arr[2] = __ldg(b + (P + 2) * W - R);                             \
+    arr[3] = __ldg(bR + (P + 3) * W + 1);                            \
+    arr[4] = __ldg(b + (P + 4) * W + R);                             \
+    arr[5] = __ldg(bL + (P + 5) * W - R - 1);                        \
+    arr[6] = __ldg(bR + (P + 6) * W - R + 1);                        \
+    arr[7] = __ldg(bR + (P + 7) * W + R + 1);                        \
+    arr[8] = __ldg(bL + (P + 8) * W + R - 1);
+    BTRIRT_PULL(9, g)
+    if (FLOW) {
+        BTRIRT_PULL(0, f)
+    }
+#undef BTRIRT_PULL
+}
+
+// Any cell: explicit source test per direction and the wall rules.
+template <typename real, int PROB, bool FLOW>
+__device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y, real f[9],
+                                         real g[9], real &q) {
+    const long long self = pop_index(x, y, 0, a.ny);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        int sx = x - cx, sy = y - cy;
+        if (PROB == kStefan) sy = (sy < 0) ? sy + a.ny : ((sy >= a.ny) ? sy - a.ny : sy);
+        const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
+        const long long cell = in ? pop_index(sx, sy, 0, a.ny) : self;
+        const int pl = in ? i : opp_of(i);
+        real gv = __ldg(a.src + cell + (9 + pl) * kTW);
+        if (FLOW) f[i] = __ldg(a.src + cell + pl * kTW);
+        if (!in) {
+            bool heated;
+            if (PROB == kStefan) {
+                heated = sx < 0;
+            } else {
+                const int xc2 = 2 * x + 1 - cx;  // twice the wall-crossing abscissa
+                heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
+            }
+            if (heated) {
+                const real wt = real(2) * w_of<real>(i);  // 2 w_i C_p T_h, T_h = 1
+                q += wt - real(2) * gv;
+                gv = wt - gv;
+            }
+        }
+        g[i] = gv;
+    }
+}
+
+// ---- reductions ----
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;
 }
 
-// Sums (kind 0) or maxes (kind 1) NV values across the block; result valid in
-// thread 0.  `sh` holds 32 * NV doubles.
+// Sums (kind 0) or maxes (kind 1) NV doubles over the block, one value per
+// warp (lane 0 holds it); result valid in thread 0.  `sh` holds 32*NV doubles.
 template <int NV>
-__device__ __forceinline__ void block_reduce(double (&v)[NV], const int (&kind)[NV],
-                                             double *sh) {
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int nthreads = blockDim.x * blockDim.y;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = (nthreads + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = kind[k] ? warp_max(v[k]) : warp_sum(v[k]);
+__device__ __forceinline__ void block_fold(double (&v)[NV], const int (&kind)[NV], double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) sh[k * 32 + warp] = v[k];
@@ -111,152 +265,124 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], const int (&kind)[
             v[k] = kind[k] ? warp_max(x) : warp_sum(x);
         }
     }
+    __syncthreads();
 }
 
-// ---- per-cell streaming ----
-template <typename real, int PROB, bool FLOW>
-__device__ __forceinline__ void pull_cell(const SweepArgs<real> &a, int x, int y, real f[9],
-                                          real g[9], real &q) {
-    const real th2 = real(2);  // 2 T_h with T_h = 1
+// Per-block diagnostics partials -> the record.  The last block to take a
+// ticket folds all partials in block order (deterministic) and resets the
+// counter; partials are read with ld.global.cg so L1 cannot serve stale lines.
+__device__ __forceinline__ void diag_finish(double (&v)[4], double *dpart, unsigned *dcount,
+                                            DevRecord *rec, double step, bool init, double *sh) {
+    const int kind[4] = {0, 0, 1, 1};
+    block_fold<4>(v, kind, sh);
+    const unsigned nblk = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i);
-        int sx = x - cx, sy = y - cy;
-        if (PROB == kStefan) sy = (sy < 0) ? sy + a.ny : ((sy >= a.ny) ? sy - a.ny : sy);
-        const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
-        const long long cell = in ? (long long)sy * a.pitch + sx : (long long)y * a.pitch + x;
-        const int pl = in ? i : opp_of(i);
-        real gv = __ldg(a.src + (long long)(9 + pl) * a.pstride + cell);
-        if (FLOW) f[i] = __ldg(a.src + (long long)pl * a.pstride + cell);
-        if (!in) {
-            bool heated;
-            if (PROB == kStefan) {
-                heated = sx < 0;
-            } else {
-                const int xc2 = 2 * x + 1 - cx;  // twice the wall-crossing abscissa
-                heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
-            }
-            if (heated) {
-                const real wt = w_of<real>(i) * th2;
-                q += wt - real(2) * gv;
-                gv = wt - gv;
-            }
+        for (int k = 0; k < 4; ++k) dpart[4 * (size_t)bid + k] = v[k];
+        __threadfence();
+        last = atomicAdd(dcount, 1u) == nblk - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const double2 s01 = __ldcg(reinterpret_cast<const double2 *>(dpart + 4 * (size_t)b));
+        const double2 s23 = __ldcg(reinterpret_cast<const double2 *>(dpart + 4 * (size_t)b + 2));
+        acc[0] += s01.x;
+        acc[1] += s01.y;
+        acc[2] = fmax(acc[2], s23.x);
+        acc[3] = fmax(acc[3], s23.y);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
+    block_fold<4>(acc, kind, sh);
+    if (threadIdx.x == 0) {
+        rec->step = step;
+        rec->melt_sum = acc[0];
+        rec->H_sum = acc[1];
+        rec->max_u = acc[2];
+        rec->nan_flag = acc[3];
+        rec->valid = 1.0;
+        if (init) {
+            rec->Q_last = 0.0;
+            rec->Q_cum = 0.0;
         }
-        g[i] = gv;
+        *dcount = 0u;
     }
 }
 
+// ---- the sweep ----
 template <typename real, int PROB, bool FLOW, int MODE>
-__global__ void __launch_bounds__(256) lattice_kernel(const SweepArgs<real> a) {
+__global__ void __launch_bounds__(kTW) lattice_kernel(const SweepArgs<real> a) {
     __shared__ double sh[32 * 4];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool active = x < a.nx && y < a.ny;
+    const int lx = threadIdx.x;
+    const int x = blockIdx.x * kTW + lx;
+    const int y0 = blockIdx.y * a.rows;
+    const int y1 = min(y0 + a.rows, a.ny);
+    const bool active = x < a.nx;
+    // the warp's 32 columns are clear of both side walls (warp-uniform)
+    const int xw = blockIdx.x * kTW + (lx & ~31);
+    const bool fastcol = xw >= 1 && xw + 31 <= a.nx - 2;
+
+    long long i0 = 0, iL = 0, iR = 0;
+    if (fastcol) {
+        i0 = pop_index(x, y0, 0, a.ny);
+        iL = (lx == 0) ? pop_index(x - 1, y0, 0, a.ny) + 1 : i0;
+        iR = (lx == kTW - 1) ? pop_index(x + 1, y0, 0, a.ny) - 1 : i0;
+    }
 
     real q = real(0);
-    real H = real(0), T = real(0), fl = real(0), rho = real(1), ux = real(0), uy = real(0);
-    if (active) {
+    real sfl = real(0), sH = real(0), umax2 = real(0);
+    bool bad = false;
+    for (int y = y0; y < y1; ++y, i0 += kRS, iL += kRS, iR += kRS) {
+        if (!active) continue;
         real f[9], g[9];
-        pull_cell<real, PROB, FLOW>(a, x, y, f, g, q);
-
-        // flow moments
-        real jx = real(0), jy = real(0);
-        if (FLOW) {
-            rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-            jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-            jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        }
-        // total enthalpy and its inversion (H_s = 0, H_l = L)
-        H = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-        if (H <= real(0)) {
-            T = H;
-            fl = real(0);
-        } else if (H >= a.Lh) {
-            T = H - a.Lh;
-            fl = real(1);
+        if (fastcol && y >= 1 && y <= a.ny - 2) {
+            pull_fast<real, FLOW>(a.src + i0, a.src + iL, a.src + iR, f, g);
         } else {
-            T = real(0);
-            fl = H / a.Lh;
+            pull_any<real, PROB, FLOW>(a, x, y, f, g, q);
         }
-        // buoyancy and solid treatment
-        real Fy = real(0);
-        if (FLOW) {
-            Fy = a.gbeta * T;
-            const real inv_rho = real(1) / rho;
-            ux = fl * jx * inv_rho;
-            uy = fl * (jy + real(0.5) * Fy) * inv_rho;
-        }
-
         if (MODE == kFields) {
+            const Macro<real> m = cell_update<real, FLOW, false>(a, f, g);
             const long long o = (long long)y * a.nx + x;
-            if (a.oH) a.oH[o] = (double)H;
-            if (a.oT) a.oT[o] = (double)T;
-            if (a.oFL) a.oFL[o] = (double)fl;
-            if (a.oUX) a.oUX[o] = (double)ux;
-            if (a.oUY) a.oUY[o] = (double)uy;
-            if (a.oRHO) a.oRHO[o] = (double)rho;
-        } else {
-            // g collision (Eq. 2, Eq. 4)
-            {
-                real n[9];
-                const real w0T = w_of<real>(0) * T;
-                n[0] = g[0] - (H - T + w0T);
+            if (a.oH) a.oH[o] = (double)m.H;
+            if (a.oT) a.oT[o] = (double)m.T;
+            if (a.oFL) a.oFL[o] = (double)m.fl;
+            if (a.oUX) a.oUX[o] = (double)m.ux;
+            if (a.oUY) a.oUY[o] = (double)m.uy;
+            if (a.oRHO) a.oRHO[o] = (double)m.rho;
+            continue;
+        }
+        const Macro<real> m = cell_update<real, FLOW, true>(a, f, g);
+        real *d = a.dst + pop_index(x, y, 0, a.ny);
 #pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    const real cu = real(cx_of(i)) * ux + real(cy_of(i)) * uy;
-                    n[i] = g[i] - w_of<real>(i) * T * (real(1) + real(3) * cu);
-                }
-                real m1x, m1y, m2xx, m2xy, m2yy;
-                moments<real>(n, m1x, m1y, m2xx, m2xy, m2yy);
-                const real d1 = a.k1 - a.k0, d2 = a.k2 - a.k0;
-                block_relax<real>(g, n, a.k0, d1 * m1x, d1 * m1y, d2 * m2xx, d2 * m2xy,
-                                  d2 * m2yy);
-            }
-            // f collision with forcing
-            if (FLOW) {
-                real n[9];
-                const real uu = ux * ux + uy * uy;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const real cu = real(cx_of(i)) * ux + real(cy_of(i)) * uy;
-                    n[i] = f[i] - w_of<real>(i) * rho *
-                                      (real(1) + real(3) * cu + real(4.5) * cu * cu -
-                                       real(1.5) * uu);
-                }
-                real m1x, m1y, m2xx, m2xy, m2yy;
-                moments<real>(n, m1x, m1y, m2xx, m2xy, m2yy);
-                const real d1 = a.k1f - a.k0f, d2 = a.k2f - a.k0f;
-                const real s1 = real(1) - real(0.5) * a.k1f, s2 = real(1) - real(0.5) * a.k2f;
-                block_relax<real>(f, n, a.k0f, d1 * m1x, d1 * m1y - s1 * Fy, d2 * m2xx,
-                                  d2 * m2xy - s2 * ux * Fy, d2 * m2yy - s2 * real(2) * uy * Fy);
-            }
-            const long long cell = (long long)y * a.pitch + x;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                a.dst[(long long)(9 + i) * a.pstride + cell] = g[i];
-                if (FLOW) a.dst[(long long)i * a.pstride + cell] = f[i];
-            }
+        for (int i = 0; i < 9; ++i) {
+            d[(9 + i) * kTW] = g[i];
+            if (FLOW) d[i * kTW] = f[i];
+        }
+        if (MODE == kSweepDiag) {
+            sfl += m.fl;
+            sH += m.H;
+            umax2 = max(umax2, m.ux * m.ux + m.uy * m.uy);
+            bad |= !(isfinite(m.H) && isfinite(m.rho));
         }
     }
-
     if (MODE == kFields) return;
 
     // ---- heated-wall inflow of this step (blocks touching the T_h wall) ----
-    // Each such block writes one partial; the last block to take a ticket
-    // folds them in slot order (deterministic) and resets the counter.
-    // Partials are read with ld.global.cg so that L1 cannot serve stale data.
     const bool qblock = (PROB == kCavity) ? (a.strip_on && blockIdx.y == 0) : (blockIdx.x == 0);
     if (qblock) {
-        double v[1] = {(double)q};
         const int kind[1] = {0};
-        block_reduce<1>(v, kind, sh);
-        const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-        if (tid == 0) {
+        double v[1] = {warp_sum((double)q)};
+        block_fold<1>(v, kind, sh);
+        if (threadIdx.x == 0) {
             const int slot = (PROB == kCavity) ? blockIdx.x : blockIdx.y;
             a.qpart[slot] = v[0];
             __threadfence();
-            const unsigned ticket = atomicAdd(a.qcount, 1u);
-            if (ticket == (unsigned)a.nq - 1u) {
+            if (atomicAdd(a.qcount, 1u) == (unsigned)a.nq - 1u) {
                 __threadfence();
                 double s = 0.0;
                 for (int k = 0; k < a.nq; ++k) s += __ldcg(a.qpart + k);
@@ -265,50 +391,14 @@ __global__ void __launch_bounds__(256) lattice_kernel(const SweepArgs<real> a) {
                 *a.qcount = 0u;
             }
         }
-        __syncthreads();
     }
 
-    // ---- diagnostics of this step ----
+    // ---- diagnostics: sums within the warp in the working precision (32
+    // threads x `rows` cells), then FP64 across warps and blocks ----
     if (MODE == kSweepDiag) {
-        const real um = sqrt(ux * ux + uy * uy);
-        const bool bad = active && !(isfinite((double)H) && isfinite((double)rho));
-        double v[4] = {active ? (double)fl : 0.0, active ? (double)H : 0.0,
-                       active ? (double)um : 0.0, bad ? 1.0 : 0.0};
-        const int kind[4] = {0, 0, 1, 1};
-        block_reduce<4>(v, kind, sh);
-        const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-        const unsigned nblk = gridDim.x * gridDim.y;
-        const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
-        __shared__ bool last;
-        if (tid == 0) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) a.dpart[4 * (size_t)bid + k] = v[k];
-            __threadfence();
-            last = atomicAdd(a.dcount, 1u) == nblk - 1u;
-        }
-        __syncthreads();
-        if (last) {
-            __threadfence();
-            const int nthreads = blockDim.x * blockDim.y;
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
-            for (unsigned b = tid; b < nblk; b += nthreads) {
-                acc[0] += __ldcg(a.dpart + 4 * (size_t)b + 0);
-                acc[1] += __ldcg(a.dpart + 4 * (size_t)b + 1);
-                acc[2] = fmax(acc[2], __ldcg(a.dpart + 4 * (size_t)b + 2));
-                acc[3] = fmax(acc[3], __ldcg(a.dpart + 4 * (size_t)b + 3));
-            }
-            __syncthreads();
-            block_reduce<4>(acc, kind, sh);
-            if (tid == 0) {
-                a.rec->step = (double)a.step;
-                a.rec->melt_sum = acc[0];
-                a.rec->H_sum = acc[1];
-                a.rec->max_u = acc[2];
-                a.rec->nan_flag = acc[3];
-                a.rec->valid = 1.0;
-                *a.dcount = 0u;
-            }
-        }
+        double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH),
+                       (double)sqrt(warp_max(umax2)), (double)warp_max(bad ? 1 : 0)};
+        diag_finish(v, a.dpart, a.dcount, a.rec, (double)a.step, false, sh);
     }
 }
 
@@ -325,111 +415,89 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t v) {
 // of T), f_i = w_i, g_i = g_eq(H0, T(H0), u = 0) (Eq. 4); reduces the step-0
 // diagnostics.
 template <typename real>
-__global__ void __launch_bounds__(256) init_kernel(const SweepArgs<real> a, double amp,
+__global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, double amp,
                                                    uint64_t seed) {
     __shared__ double sh[32 * 4];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool active = x < a.nx && y < a.ny;
-    real H = real(0), fl = real(0);
-    if (active) {
-        const uint64_t cell = (uint64_t)y * (uint64_t)a.nx + (uint64_t)x;
-        const double r = (double)(splitmix64(seed ^ cell) >> 11) * 0x1.0p-53;
-        H = (real)(amp * (2.0 * r - 1.0));
-        real T;
-        if (H <= real(0)) {
-            T = H;
-            fl = real(0);
-        } else if (H >= a.Lh) {
-            T = H - a.Lh;
-            fl = real(1);
-        } else {
-            T = real(0);
-            fl = H / a.Lh;
-        }
-        const long long c = (long long)y * a.pitch + x;
-        a.dst[9 * a.pstride + c] = H - T + w_of<real>(0) * T;
+    const int x = blockIdx.x * kTW + threadIdx.x;
+    const int y0 = blockIdx.y * a.rows;
+    const int y1 = min(y0 + a.rows, a.ny);
+    real sfl = real(0), sH = real(0);
+    bool bad = false;
+    if (x < a.nx) {
+        for (int y = y0; y < y1; ++y) {
+            const uint64_t cell = (uint64_t)y * (uint64_t)a.nx + (uint64_t)x;
+            const double r = (double)(splitmix64(seed ^ cell) >> 11) * 0x1.0p-53;
+            const real H = (real)(amp * (2.0 * r - 1.0));
+            real T, fl;
+            invert(H, a.Lh, T, fl);
+            const long long c = pop_index(x, y, 0, a.ny);
+            a.dst[c + 9 * kTW] = H - T + w_of<real>(0) * T;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) a.dst[(long long)(9 + i) * a.pstride + c] = w_of<real>(i) * T;
+            for (int i = 1; i < 9; ++i) a.dst[c + (9 + i) * kTW] = w_of<real>(i) * T;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            a.dst[(long long)i * a.pstride + c] = w_of<real>(i);
-            if (a.aux) a.aux[(long long)i * a.pstride + c] = w_of<real>(i);
+            for (int i = 0; i < 9; ++i) {
+                a.dst[c + i * kTW] = w_of<real>(i);
+                if (a.aux) a.aux[c + i * kTW] = w_of<real>(i);
+            }
+            sfl += fl;
+            sH += H;
+            bad |= !isfinite(H);
         }
     }
-    const bool bad = active && !isfinite((double)H);
-    double v[4] = {(double)fl, (double)H, 0.0, bad ? 1.0 : 0.0};
-    const int kind[4] = {0, 0, 1, 1};
-    block_reduce<4>(v, kind, sh);
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const unsigned nblk = gridDim.x * gridDim.y;
-    const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
-    __shared__ bool last;
-    if (tid == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a.dpart[4 * (size_t)bid + k] = v[k];
-        __threadfence();
-        last = atomicAdd(a.dcount, 1u) == nblk - 1u;
-    }
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        const int nthreads = blockDim.x * blockDim.y;
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (unsigned b = tid; b < nblk; b += nthreads) {
-            acc[0] += __ldcg(a.dpart + 4 * (size_t)b + 0);
-            acc[1] += __ldcg(a.dpart + 4 * (size_t)b + 1);
-            acc[3] = fmax(acc[3], __ldcg(a.dpart + 4 * (size_t)b + 3));
-        }
-        __syncthreads();
-        block_reduce<4>(acc, kind, sh);
-        if (tid == 0) {
-            a.rec->step = 0.0;
-            a.rec->melt_sum = acc[0];
-            a.rec->H_sum = acc[1];
-            a.rec->Q_last = 0.0;
-            a.rec->Q_cum = 0.0;
-            a.rec->max_u = 0.0;
-            a.rec->nan_flag = acc[3];
-            a.rec->valid = 1.0;
-            *a.dcount = 0u;
-        }
-    }
+    double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH), 0.0, (double)warp_max(bad ? 1 : 0)};
+    diag_finish(v, a.dpart, a.dcount, a.rec, 0.0, true, sh);
 }
 
 // Fields of the step-0 state (no streaming; u = 0 by definition).
 template <typename real, bool FLOW>
-__global__ void __launch_bounds__(256) fields0_kernel(const SweepArgs<real> a) {
+__global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
+    const int x = blockIdx.x * kTW + threadIdx.x;
+    const int y0 = blockIdx.y * a.rows;
+    const int y1 = min(y0 + a.rows, a.ny);
+    if (x >= a.nx) return;
+    for (int y = y0; y < y1; ++y) {
+        const long long c = pop_index(x, y, 0, a.ny);
+        real g[9], H, rho = real(1);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = a.src[c + (9 + i) * kTW];
+        H = sum9(g);
+        if (FLOW) {
+            real f[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = a.src[c + i * kTW];
+            rho = sum9(f);
+        }
+        real T, fl;
+        invert(H, a.Lh, T, fl);
+        const long long o = (long long)y * a.nx + x;
+        if (a.oH) a.oH[o] = (double)H;
+        if (a.oT) a.oT[o] = (double)T;
+        if (a.oFL) a.oFL[o] = (double)fl;
+        if (a.oUX) a.oUX[o] = 0.0;
+        if (a.oUY) a.oUY[o] = 0.0;
+        if (a.oRHO) a.oRHO[o] = (double)rho;
+    }
+}
+
+// Tile-major <-> plane-major FP64 staging, one thread per cell.
+template <typename real>
+__global__ void repack_kernel(real *buf, real *buf2, double *stage, int nx, int ny,
+                              bool to_staging) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
-    const long long c = (long long)y * a.pitch + x;
-    real H = real(0), rho = real(1);
+    const int y = blockIdx.y;
+    if (x >= nx) return;
+    const long long c = pop_index(x, y, 0, ny);
+    const long long P = (long long)nx * ny, o = (long long)y * nx + x;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) H += a.src[(long long)(9 + i) * a.pstride + c];
-    if (FLOW) {
-        rho = real(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) rho += a.src[(long long)i * a.pstride + c];
+    for (int p = 0; p < kPlanes; ++p) {
+        if (to_staging) {
+            stage[p * P + o] = (double)buf[c + p * kTW];
+        } else {
+            const real v = (real)stage[p * P + o];
+            buf[c + p * kTW] = v;
+            if (buf2 && p < 9) buf2[c + p * kTW] = v;
+        }
     }
-    real T, fl;
-    if (H <= real(0)) {
-        T = H;
-        fl = real(0);
-    } else if (H >= a.Lh) {
-        T = H - a.Lh;
-        fl = real(1);
-    } else {
-        T = real(0);
-        fl = H / a.Lh;
-    }
-    const long long o = (long long)y * a.nx + x;
-    if (a.oH) a.oH[o] = (double)H;
-    if (a.oT) a.oT[o] = (double)T;
-    if (a.oFL) a.oFL[o] = (double)fl;
-    if (a.oUX) a.oUX[o] = 0.0;
-    if (a.oUY) a.oUY[o] = 0.0;
-    if (a.oRHO) a.oRHO[o] = (double)rho;
 }
 
 // ---- launch dispatch (instantiated per precision in sweep_fp32/64.cu) ----
@@ -471,6 +539,14 @@ cudaError_t launch_fields0(const SweepArgs<real> &a, bool flow, dim3 grid, dim3 
         fields0_kernel<real, true><<<grid, block, 0, s>>>(a);
     else
         fields0_kernel<real, false><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_repack(real *buf, real *buf2, double *stage, int nx, int ny, bool to_staging,
+                          cudaStream_t s) {
+    dim3 block(256), grid((nx + 255) / 256, ny);
+    repack_kernel<real><<<grid, block, 0, s>>>(buf, buf2, stage, nx, ny, to_staging);
     return cudaGetLastError();
 }
 
