@@ -67,7 +67,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static",
-           "-Xlinker", "--version-script=" + os.path.join(CSRC, "exports.map"), "-o", tmp, *objs]
+           "-Xlinker", "--version-script=" + os.path.join(CSRC, "exports.map"),
+           "-Xlinker", "--no-undefined", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

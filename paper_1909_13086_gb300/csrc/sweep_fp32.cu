@@ -8,4 +8,5 @@ template cudaError_t launch_init<float>(const SweepArgs<float> &, double, uint64
                                         cudaStream_t);
 template cudaError_t launch_fields0<float>(const SweepArgs<float> &, bool, dim3, dim3,
                                            cudaStream_t);
+template cudaError_t launch_repack<float>(float *, float *, double *, int, int, bool, cudaStream_t);
 }  // namespace btrirt

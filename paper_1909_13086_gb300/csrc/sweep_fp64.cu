@@ -8,4 +8,5 @@ template cudaError_t launch_init<double>(const SweepArgs<double> &, double, uint
                                          dim3, cudaStream_t);
 template cudaError_t launch_fields0<double>(const SweepArgs<double> &, bool, dim3, dim3,
                                             cudaStream_t);
+template cudaError_t launch_repack<double>(double *, double *, double *, int, int, bool, cudaStream_t);
 }  // namespace btrirt
