@@ -136,7 +136,7 @@ int lbm_step(lbm_handle h, long long n);
 int lbm_set_diag_every(lbm_handle h, long long k);
 
 /* Launch shape: rows of the lattice walked by each thread of a block (1 to
- * 1024, default 4).  Results do not depend on it except for the rounding of
+ * 1024, default 1).  Results do not depend on it except for the rounding of
  * the FP32 in-warp diagnostic partial sums.  Used by the tuner. */
 int lbm_set_rows_per_block(lbm_handle h, int rows);
 

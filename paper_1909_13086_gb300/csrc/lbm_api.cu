@@ -14,7 +14,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "lbm_internal.h"
 
 using namespace btrirt;
@@ -27,7 +27,7 @@ lbm_alloc_fn g_alloc = nullptr;
 lbm_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
 
-constexpr int kDefaultRows = 4;  // rows walked by each thread of a block
+constexpr int kDefaultRows = 1;  // rows walked by each thread of a block (tuned on GB300)
 
 }  // namespace
 
