@@ -50,8 +50,8 @@ struct lbm_s {
     dim3 block, grid;
     // scratch: reduction partials, tickets, record; allocated once
     void *scratch = nullptr;
-    double *qpart = nullptr, *dpart = nullptr;
-    unsigned *counters = nullptr;
+    double *qpart = nullptr, *dpart = nullptr, *gpart = nullptr;
+    unsigned *counters = nullptr, *gcount = nullptr;
     DevRecord *rec = nullptr;
     int nq = 0;
     // FP64 staging for field and population read-back / write (18 x nx*ny
@@ -151,6 +151,8 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.qcount = h->counters;
     a.nq = h->nq;
     a.dpart = h->dpart;
+    a.gpart = h->gpart;
+    a.gcount = h->gcount;
     a.dcount = h->counters + 1;
     a.rec = h->rec;
     a.step = h->step;
@@ -319,11 +321,15 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
                            buffer_bytes(h));
         }
     }
-    // reduction scratch: q partials, diag partials, 2 counters, record
-    // sized for the largest grid any rows-per-block setting can produce (1 row)
+    // reduction scratch, carved from one allocation (each piece 256 B aligned):
+    // 2 counters | record | q partials | block partials | group partials |
+    // group counters.  Sized for the largest grid any rows setting gives.
     const size_t nblk = (size_t)h->ntx * (size_t)ny;
     const size_t nqmax = (size_t)(h->ntx > ny ? h->ntx : ny);
-    const size_t bytes = 256 + sizeof(DevRecord) + 256 + nqmax * 8 + nblk * 4 * 8 + 256;
+    const size_t ngrp = (nblk + 31) / 32;  // groups are >= 32 blocks
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t o_rec = 256, o_q = o_rec + up(sizeof(DevRecord)), o_d = o_q + up(nqmax * 8),
+                 o_g = o_d + up(nblk * 32), o_gc = o_g + up(ngrp * 32), bytes = o_gc + up(ngrp * 4);
     h->scratch = dev_alloc(h, bytes);
     if (!h->scratch) {
         lbm_destroy(h);
@@ -331,9 +337,11 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     }
     char *s = static_cast<char *>(h->scratch);
     h->counters = reinterpret_cast<unsigned *>(s);
-    h->rec = reinterpret_cast<DevRecord *>(s + 256);
-    h->qpart = reinterpret_cast<double *>(s + 512);
-    h->dpart = reinterpret_cast<double *>(s + 512 + ((nqmax * 8 + 255) / 256) * 256);
+    h->rec = reinterpret_cast<DevRecord *>(s + o_rec);
+    h->qpart = reinterpret_cast<double *>(s + o_q);
+    h->dpart = reinterpret_cast<double *>(s + o_d);
+    h->gpart = reinterpret_cast<double *>(s + o_g);
+    h->gcount = reinterpret_cast<unsigned *>(s + o_gc);
     e = cudaMemsetAsync(h->scratch, 0, bytes, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {

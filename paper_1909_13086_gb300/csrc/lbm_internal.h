@@ -23,7 +23,7 @@ enum Mode {
 //     index(x, y, p) = ((x / kTW) * ny + y) * 18 * kTW + p * kTW + x % kTW.
 // A warp's 18 loads of one cell row are then one base register plus
 // compile-time offsets (plane p: p*kTW; row above / below: -/+ 18*kTW).
-constexpr int kTW = 256;
+constexpr int kTW = 128;  // tile width = threads per block (fastest of 128/256/512 on GB300)
 constexpr int kPlanes = 18;
 constexpr int kRS = kPlanes * kTW;  // elements per tile row
 
@@ -62,9 +62,12 @@ struct SweepArgs {
     double *qpart;         // one partial per wall-adjacent block
     unsigned *qcount;      // ticket counter, reset to 0 by the last block
     int nq;                // number of wall-adjacent blocks
-    // diagnostics reduction (kSweepDiag, init)
+    // diagnostics reduction (kSweepDiag, init): blocks are folded in groups of
+    // blockDim.x, then the group partials are folded
     double *dpart;         // 4 partials per block
-    unsigned *dcount;      // ticket counter, reset to 0 by the last block
+    double *gpart;         // 4 partials per group
+    unsigned *gcount;      // one ticket counter per group, reset by its folder
+    unsigned *dcount;      // ticket counter over groups, reset by the last folder
     DevRecord *rec;
     long long step;        // step index the launch produces
     // field outputs (kFields), nx*ny doubles each, row-major; NULL = skip

@@ -268,38 +268,71 @@ __device__ __forceinline__ void block_fold(double (&v)[NV], const int (&kind)[NV
     __syncthreads();
 }
 
-// Per-block diagnostics partials -> the record.  The last block to take a
-// ticket folds all partials in block order (deterministic) and resets the
-// counter; partials are read with ld.global.cg so L1 cannot serve stale lines.
-__device__ __forceinline__ void diag_finish(double (&v)[4], double *dpart, unsigned *dcount,
-                                            DevRecord *rec, double step, bool init, double *sh) {
+// Per-block diagnostics partials -> the record, in two deterministic levels:
+// blocks are grouped by consecutive id into groups of blockDim.x; the last
+// block of a group to take its group ticket folds the group's partials (one
+// per thread) and takes a ticket on the group counter; the last group folder
+// folds the group partials and writes the record.  Fold order is fixed, so
+// the record is bitwise reproducible for a given launch shape.  Partials are
+// read with ld.global.cg so that L1 cannot serve stale lines; every counter is
+// reset by the block that consumed it.
+__device__ __forceinline__ void fold_loaded(double (&acc)[4], double *sh) {
     const int kind[4] = {0, 0, 1, 1};
-    block_fold<4>(v, kind, sh);
-    const unsigned nblk = gridDim.x * gridDim.y;
-    const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dpart[4 * (size_t)bid + k] = v[k];
-        __threadfence();
-        last = atomicAdd(dcount, 1u) == nblk - 1u;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const double2 s01 = __ldcg(reinterpret_cast<const double2 *>(dpart + 4 * (size_t)b));
-        const double2 s23 = __ldcg(reinterpret_cast<const double2 *>(dpart + 4 * (size_t)b + 2));
+    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
+    block_fold<4>(acc, kind, sh);
+}
+
+__device__ __forceinline__ void load_partials(double (&acc)[4], const double *part, unsigned first,
+                                              unsigned count) {
+    acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+    for (unsigned k = threadIdx.x; k < count; k += blockDim.x) {
+        const double2 s01 = __ldcg(reinterpret_cast<const double2 *>(part + 4 * (size_t)(first + k)));
+        const double2 s23 = __ldcg(reinterpret_cast<const double2 *>(part + 4 * (size_t)(first + k) + 2));
         acc[0] += s01.x;
         acc[1] += s01.y;
         acc[2] = fmax(acc[2], s23.x);
         acc[3] = fmax(acc[3], s23.y);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
-    block_fold<4>(acc, kind, sh);
+}
+
+template <typename real>
+__device__ __forceinline__ void diag_finish(double (&v)[4], const SweepArgs<real> &a, double step,
+                                            bool init, double *sh) {
+    const int kind[4] = {0, 0, 1, 1};
+    block_fold<4>(v, kind, sh);
+    const unsigned nblk = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
+    const unsigned G = blockDim.x;
+    const unsigned grp = bid / G, ngrp = (nblk + G - 1) / G;
+    const unsigned members = min(G, nblk - grp * G);
+    __shared__ bool last;
     if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.dpart[4 * (size_t)bid + k] = v[k];
+        __threadfence();
+        last = atomicAdd(a.gcount + grp, 1u) == members - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[4];
+    load_partials(acc, a.dpart, grp * G, members);
+    fold_loaded(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gpart[4 * (size_t)grp + k] = acc[k];
+        a.gcount[grp] = 0u;
+        __threadfence();
+        last = atomicAdd(a.dcount, 1u) == ngrp - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    load_partials(acc, a.gpart, 0, ngrp);
+    fold_loaded(acc, sh);
+    if (threadIdx.x == 0) {
+        DevRecord *rec = a.rec;
         rec->step = step;
         rec->melt_sum = acc[0];
         rec->H_sum = acc[1];
@@ -310,7 +343,7 @@ __device__ __forceinline__ void diag_finish(double (&v)[4], double *dpart, unsig
             rec->Q_last = 0.0;
             rec->Q_cum = 0.0;
         }
-        *dcount = 0u;
+        *a.dcount = 0u;
     }
 }
 
@@ -378,16 +411,23 @@ __global__ void __launch_bounds__(kTW) lattice_kernel(const SweepArgs<real> a) {
         const int kind[1] = {0};
         double v[1] = {warp_sum((double)q)};
         block_fold<1>(v, kind, sh);
+        __shared__ bool qlast;
         if (threadIdx.x == 0) {
             const int slot = (PROB == kCavity) ? blockIdx.x : blockIdx.y;
             a.qpart[slot] = v[0];
             __threadfence();
-            if (atomicAdd(a.qcount, 1u) == (unsigned)a.nq - 1u) {
-                __threadfence();
-                double s = 0.0;
-                for (int k = 0; k < a.nq; ++k) s += __ldcg(a.qpart + k);
-                a.rec->Q_last = s;
-                a.rec->Q_cum += s;
+            qlast = atomicAdd(a.qcount, 1u) == (unsigned)a.nq - 1u;
+        }
+        __syncthreads();
+        if (qlast) {
+            __threadfence();
+            double s = 0.0;
+            for (int k = threadIdx.x; k < a.nq; k += blockDim.x) s += __ldcg(a.qpart + k);
+            v[0] = warp_sum(s);
+            block_fold<1>(v, kind, sh);
+            if (threadIdx.x == 0) {
+                a.rec->Q_last = v[0];
+                a.rec->Q_cum += v[0];
                 *a.qcount = 0u;
             }
         }
@@ -398,7 +438,7 @@ __global__ void __launch_bounds__(kTW) lattice_kernel(const SweepArgs<real> a) {
     if (MODE == kSweepDiag) {
         double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH),
                        (double)sqrt(warp_max(umax2)), (double)warp_max(bad ? 1 : 0)};
-        diag_finish(v, a.dpart, a.dcount, a.rec, (double)a.step, false, sh);
+        diag_finish(v, a, (double)a.step, false, sh);
     }
 }
 
@@ -445,7 +485,7 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
         }
     }
     double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH), 0.0, (double)warp_max(bad ? 1 : 0)};
-    diag_finish(v, a.dpart, a.dcount, a.rec, 0.0, true, sh);
+    diag_finish(v, a, 0.0, true, sh);
 }
 
 // Fields of the step-0 state (no streaming; u = 0 by definition).
