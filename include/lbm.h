@@ -135,10 +135,12 @@ int lbm_step(lbm_handle h, long long n);
  * each lbm_step call only, the default). */
 int lbm_set_diag_every(lbm_handle h, long long k);
 
-/* Launch shape: rows of the lattice walked by each thread of a block (1 to
- * 1024, default 1).  Results do not depend on it except for the rounding of
- * the FP32 in-warp diagnostic partial sums.  Used by the tuner. */
-int lbm_set_rows_per_block(lbm_handle h, int rows);
+/* Launch shape of the sweep (the tuner's knobs): rows of the lattice walked by
+ * each thread of a block (1 to 1024, default 1), and the distance, in rows, at
+ * which each block asks L2 to prefetch a later block's tile row (0 = off).
+ * Results do not depend on either, except the rounding of the in-warp partial
+ * sums of the FP32 diagnostics.  Errors: LBM_ERR_ARG. */
+int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows);
 
 /* Bit mask selecting the fields of lbm_read_fields. */
 enum { LBM_FIELD_H = 1, LBM_FIELD_T = 2, LBM_FIELD_FL = 4, LBM_FIELD_UX = 8,

@@ -27,7 +27,8 @@ lbm_alloc_fn g_alloc = nullptr;
 lbm_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
 
-constexpr int kDefaultRows = 1;  // rows walked by each thread of a block (tuned on GB300)
+constexpr int kDefaultRows = 1;      // rows walked by each thread of a block (tuned on GB300)
+constexpr int kDefaultPrefetch = 0;  // L2 prefetch distance in rows
 
 }  // namespace
 
@@ -36,6 +37,7 @@ struct lbm_s {
     size_t esize = 4;           // bytes per population value
     int ntx = 0;                // column tiles of kTW cells
     int rows = kDefaultRows;    // rows per block
+    int prefetch = kDefaultPrefetch;  // L2 prefetch distance in rows (0 = off)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *buf[2] = {nullptr, nullptr};  // 18 planes each
@@ -136,6 +138,7 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.ny = h->ny;
     a.ntx = h->ntx;
     a.rows = h->rows;
+    a.prefetch = h->prefetch;
     a.k0 = (real)h->d.k0;
     a.k1 = (real)h->d.k1;
     a.k2 = (real)h->d.k2;
@@ -491,9 +494,11 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
     return LBM_OK;
 }
 
-int lbm_set_rows_per_block(lbm_handle h, int rows) {
-    if (!h || rows < 1 || rows > 1024) return set_err(h, LBM_ERR_ARG, "rows must be in [1, 1024]");
+int lbm_set_launch(lbm_handle h, int rows, int prefetch_rows) {
+    if (!h || rows < 1 || rows > 1024 || prefetch_rows < 0)
+        return set_err(h, LBM_ERR_ARG, "rows must be in [1, 1024] and prefetch_rows >= 0");
     h->rows = rows;
+    h->prefetch = prefetch_rows;
     set_grid(h);
     return LBM_OK;
 }

@@ -53,6 +53,8 @@ struct SweepArgs {
     int nx, ny;            // lattice size
     int ntx;               // number of column tiles
     int rows;              // rows per block (each thread walks them)
+    int prefetch;          // > 0: each block asks L2 for the tile row `prefetch`
+                           // rows below its own (one bulk prefetch per block)
     real k0, k1, k2;       // g rates (Eq. 2)
     real k0f, k1f, k2f;    // f rates
     real Lh, gbeta;        // latent heat, g*beta

@@ -347,6 +347,17 @@ __device__ __forceinline__ void diag_finish(double (&v)[4], const SweepArgs<real
     }
 }
 
+// Bulk prefetch of one contiguous tile row (all 18 planes, kRS values) into
+// L2: a single TMA-unit request, no registers or shared memory involved.  The
+// address is 16 B aligned (tile rows are kRS * sizeof(real) bytes apart from a
+// 256 B aligned base) and the size a multiple of 16.
+template <typename real>
+__device__ __forceinline__ void prefetch_tile_row_l2(const real *p) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p),
+                 "r"((unsigned)(kRS * sizeof(real)))
+                 : "memory");
+}
+
 // ---- the sweep ----
 template <typename real, int PROB, bool FLOW, int MODE>
 __global__ void __launch_bounds__(kTW) lattice_kernel(const SweepArgs<real> a) {
@@ -355,6 +366,11 @@ __global__ void __launch_bounds__(kTW) lattice_kernel(const SweepArgs<real> a) {
     const int x = blockIdx.x * kTW + lx;
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
+    // Blocks are scheduled roughly in row order, so the row `prefetch` rows
+    // ahead belongs to a block that starts a little later: fetching it into L2
+    // now shortens that block's load latency.
+    if (a.prefetch > 0 && threadIdx.x == 0 && y0 + a.prefetch < a.ny)
+        prefetch_tile_row_l2(a.src + pop_index(blockIdx.x * kTW, y0 + a.prefetch, 0, a.ny));
     const bool active = x < a.nx;
     // the warp's 32 columns are clear of both side walls (warp-uniform)
     const int xw = blockIdx.x * kTW + (lx & ~31);
