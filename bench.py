@@ -43,6 +43,15 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_13086_gb300", "csrc", f)
                   for f in ("sweep.cuh", "lbm_internal.h")]
 
 
+def sweep_launches(warmup: int, steps: int) -> int:
+    """Kernels launched by lbm_step(steps) after `warmup` steps: one sweep per
+    step, plus the one-block diagnostics fold after every diagnostic sweep
+    (every DIAG_EVERY-th step and the last one)."""
+    diag = {n for n in range(warmup + 1, warmup + steps + 1) if n % DIAG_EVERY == 0}
+    diag.add(warmup + steps)
+    return steps + len(diag)
+
+
 def workload_config(precision: str) -> dict:
     return {"workload": f"cavity {NX}x{NY}, Ra 1e8, Pr 1, Ste 1, Ma 0.1, strip W/4 centred, "
                         f"{precision.upper()} populations",
@@ -331,7 +340,7 @@ def run_ours(args) -> None:
         "config": workload_config(prec),
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": sweep_launches(args.warmup, args.steps),
         "clocks": clocks.summary(),
         "melt_fraction": d["melt_fraction"],
     }

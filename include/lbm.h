@@ -137,7 +137,8 @@ int lbm_set_diag_every(lbm_handle h, long long k);
 
 /* Launch shape of the sweep (the tuner's knobs): rows of the lattice walked by
  * each thread of a block (1 to 1024, default 1), and the distance, in rows, at
- * which each block asks L2 to prefetch a later block's tile row (0 = off).
+ * which each block asks L2 to prefetch a later block's tile row (0 = off,
+ * default 4).
  * Results do not depend on either, except the rounding of the in-warp partial
  * sums of the FP32 diagnostics.  Errors: LBM_ERR_ARG. */
 int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows);

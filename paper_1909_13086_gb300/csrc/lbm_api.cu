@@ -28,7 +28,7 @@ lbm_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
 
 constexpr int kDefaultRows = 1;      // rows walked by each thread of a block (tuned on GB300)
-constexpr int kDefaultPrefetch = 0;  // L2 prefetch distance in rows
+constexpr int kDefaultPrefetch = 4;  // L2 prefetch distance in rows (tuned on GB300)
 
 }  // namespace
 
@@ -52,8 +52,8 @@ struct lbm_s {
     dim3 block, grid;
     // scratch: reduction partials, tickets, record; allocated once
     void *scratch = nullptr;
-    double *qpart = nullptr, *dpart = nullptr, *gpart = nullptr;
-    unsigned *counters = nullptr, *gcount = nullptr;
+    double *qpart = nullptr, *dpart = nullptr;
+    unsigned *counters = nullptr;
     DevRecord *rec = nullptr;
     int nq = 0;
     // FP64 staging for field and population read-back / write (18 x nx*ny
@@ -154,9 +154,6 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.qcount = h->counters;
     a.nq = h->nq;
     a.dpart = h->dpart;
-    a.gpart = h->gpart;
-    a.gcount = h->gcount;
-    a.dcount = h->counters + 1;
     a.rec = h->rec;
     a.step = h->step;
     return a;
@@ -325,14 +322,13 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
         }
     }
     // reduction scratch, carved from one allocation (each piece 256 B aligned):
-    // 2 counters | record | q partials | block partials | group partials |
-    // group counters.  Sized for the largest grid any rows setting gives.
+    // counter | record | heated-wall partials | per-block diagnostics partials.
+    // Sized for the largest grid any rows setting gives (one row per block).
     const size_t nblk = (size_t)h->ntx * (size_t)ny;
     const size_t nqmax = (size_t)(h->ntx > ny ? h->ntx : ny);
-    const size_t ngrp = (nblk + 31) / 32;  // groups are >= 32 blocks
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t o_rec = 256, o_q = o_rec + up(sizeof(DevRecord)), o_d = o_q + up(nqmax * 8),
-                 o_g = o_d + up(nblk * 32), o_gc = o_g + up(ngrp * 32), bytes = o_gc + up(ngrp * 4);
+                 bytes = o_d + up(nblk * 32);
     h->scratch = dev_alloc(h, bytes);
     if (!h->scratch) {
         lbm_destroy(h);
@@ -343,8 +339,6 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     h->rec = reinterpret_cast<DevRecord *>(s + o_rec);
     h->qpart = reinterpret_cast<double *>(s + o_q);
     h->dpart = reinterpret_cast<double *>(s + o_d);
-    h->gpart = reinterpret_cast<double *>(s + o_g);
-    h->gcount = reinterpret_cast<unsigned *>(s + o_gc);
     e = cudaMemsetAsync(h->scratch, 0, bytes, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -378,7 +372,7 @@ int lbm_set_params(lbm_handle h, const lbm_params *p) {
     h->cur = 0;
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned), h->stream));
     rc = h->precision == LBM_FP64 ? enqueue_init<double>(h) : enqueue_init<float>(h);
     if (rc != LBM_OK) return rc;
     h->params_set = true;

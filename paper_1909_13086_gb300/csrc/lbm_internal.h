@@ -64,12 +64,9 @@ struct SweepArgs {
     double *qpart;         // one partial per wall-adjacent block
     unsigned *qcount;      // ticket counter, reset to 0 by the last block
     int nq;                // number of wall-adjacent blocks
-    // diagnostics reduction (kSweepDiag, init): blocks are folded in groups of
-    // blockDim.x, then the group partials are folded
-    double *dpart;         // 4 partials per block
-    double *gpart;         // 4 partials per group
-    unsigned *gcount;      // one ticket counter per group, reset by its folder
-    unsigned *dcount;      // ticket counter over groups, reset by the last folder
+    // diagnostics (kSweepDiag, init): 4 partials per block, folded into the
+    // record by a one-block kernel launched right after on the same stream
+    double *dpart;
     DevRecord *rec;
     long long step;        // step index the launch produces
     // field outputs (kFields), nx*ny doubles each, row-major; NULL = skip

@@ -268,71 +268,41 @@ __device__ __forceinline__ void block_fold(double (&v)[NV], const int (&kind)[NV
     __syncthreads();
 }
 
-// Per-block diagnostics partials -> the record, in two deterministic levels:
-// blocks are grouped by consecutive id into groups of blockDim.x; the last
-// block of a group to take its group ticket folds the group's partials (one
-// per thread) and takes a ticket on the group counter; the last group folder
-// folds the group partials and writes the record.  Fold order is fixed, so
-// the record is bitwise reproducible for a given launch shape.  Partials are
-// read with ld.global.cg so that L1 cannot serve stale lines; every counter is
-// reset by the block that consumed it.
-__device__ __forceinline__ void fold_loaded(double (&acc)[4], double *sh) {
+// Per-block diagnostics partials.  A sweep (or the init kernel) writes one
+// record of 4 doubles per block with plain stores -- no fence, no ticket, so a
+// block's lifetime does not grow -- and diag_reduce_kernel, launched right
+// after on the same stream, folds them in block order (deterministic for a
+// given launch shape) into the FP64 record.
+__device__ __forceinline__ void diag_partial(double (&v)[4], double *dpart, double *sh) {
     const int kind[4] = {0, 0, 1, 1};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
-    block_fold<4>(acc, kind, sh);
+    block_fold<4>(v, kind, sh);
+    if (threadIdx.x == 0) {
+        const size_t bid = blockIdx.x + (size_t)blockIdx.y * gridDim.x;
+        reinterpret_cast<double2 *>(dpart)[2 * bid] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(dpart)[2 * bid + 1] = make_double2(v[2], v[3]);
+    }
 }
 
-__device__ __forceinline__ void load_partials(double (&acc)[4], const double *part, unsigned first,
-                                              unsigned count) {
-    acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
-    for (unsigned k = threadIdx.x; k < count; k += blockDim.x) {
-        const double2 s01 = __ldcg(reinterpret_cast<const double2 *>(part + 4 * (size_t)(first + k)));
-        const double2 s23 = __ldcg(reinterpret_cast<const double2 *>(part + 4 * (size_t)(first + k) + 2));
+// One block of kReduceThreads threads: thread t folds partials t, t + T, ...
+// in order, then a fixed tree across the block.
+constexpr int kReduceThreads = 1024;
+static __global__ void __launch_bounds__(kReduceThreads)
+    diag_reduce_kernel(const double *dpart, unsigned nblk, DevRecord *rec, double step, int init) {
+    __shared__ double sh[32 * 4];
+    const int kind[4] = {0, 0, 1, 1};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const double2 s01 = reinterpret_cast<const double2 *>(dpart)[2 * (size_t)b];
+        const double2 s23 = reinterpret_cast<const double2 *>(dpart)[2 * (size_t)b + 1];
         acc[0] += s01.x;
         acc[1] += s01.y;
         acc[2] = fmax(acc[2], s23.x);
         acc[3] = fmax(acc[3], s23.y);
     }
-}
-
-template <typename real>
-__device__ __forceinline__ void diag_finish(double (&v)[4], const SweepArgs<real> &a, double step,
-                                            bool init, double *sh) {
-    const int kind[4] = {0, 0, 1, 1};
-    block_fold<4>(v, kind, sh);
-    const unsigned nblk = gridDim.x * gridDim.y;
-    const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
-    const unsigned G = blockDim.x;
-    const unsigned grp = bid / G, ngrp = (nblk + G - 1) / G;
-    const unsigned members = min(G, nblk - grp * G);
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.dpart[4 * (size_t)bid + k] = v[k];
-        __threadfence();
-        last = atomicAdd(a.gcount + grp, 1u) == members - 1u;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double acc[4];
-    load_partials(acc, a.dpart, grp * G, members);
-    fold_loaded(acc, sh);
+    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
+    block_fold<4>(acc, kind, sh);
     if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a.gpart[4 * (size_t)grp + k] = acc[k];
-        a.gcount[grp] = 0u;
-        __threadfence();
-        last = atomicAdd(a.dcount, 1u) == ngrp - 1u;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    load_partials(acc, a.gpart, 0, ngrp);
-    fold_loaded(acc, sh);
-    if (threadIdx.x == 0) {
-        DevRecord *rec = a.rec;
         rec->step = step;
         rec->melt_sum = acc[0];
         rec->H_sum = acc[1];
@@ -343,7 +313,6 @@ __device__ __forceinline__ void diag_finish(double (&v)[4], const SweepArgs<real
             rec->Q_last = 0.0;
             rec->Q_cum = 0.0;
         }
-        *a.dcount = 0u;
     }
 }
 
@@ -454,7 +423,7 @@ __global__ void __launch_bounds__(kTW) lattice_kernel(const SweepArgs<real> a) {
     if (MODE == kSweepDiag) {
         double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH),
                        (double)sqrt(warp_max(umax2)), (double)warp_max(bad ? 1 : 0)};
-        diag_finish(v, a, (double)a.step, false, sh);
+        diag_partial(v, a.dpart, sh);
     }
 }
 
@@ -501,7 +470,7 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
         }
     }
     double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH), 0.0, (double)warp_max(bad ? 1 : 0)};
-    diag_finish(v, a, 0.0, true, sh);
+    diag_partial(v, a.dpart, sh);
 }
 
 // Fields of the step-0 state (no streaming; u = 0 by definition).
@@ -571,21 +540,35 @@ static cudaError_t launch_mode(const SweepArgs<real> &a, int mode, dim3 grid, di
     return cudaGetLastError();
 }
 
+static cudaError_t launch_diag_reduce(const double *dpart, dim3 grid, DevRecord *rec,
+                                      long long step, bool init, cudaStream_t s) {
+    diag_reduce_kernel<<<1, kReduceThreads, 0, s>>>(dpart, grid.x * grid.y, rec, (double)step,
+                                                    init ? 1 : 0);
+    return cudaGetLastError();
+}
+
 template <typename real>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
                            dim3 grid, dim3 block, cudaStream_t s) {
+    cudaError_t e;
     if (problem == kCavity)
-        return flow ? launch_mode<real, kCavity, true>(a, mode, grid, block, s)
-                    : launch_mode<real, kCavity, false>(a, mode, grid, block, s);
-    return flow ? launch_mode<real, kStefan, true>(a, mode, grid, block, s)
-                : launch_mode<real, kStefan, false>(a, mode, grid, block, s);
+        e = flow ? launch_mode<real, kCavity, true>(a, mode, grid, block, s)
+                 : launch_mode<real, kCavity, false>(a, mode, grid, block, s);
+    else
+        e = flow ? launch_mode<real, kStefan, true>(a, mode, grid, block, s)
+                 : launch_mode<real, kStefan, false>(a, mode, grid, block, s);
+    if (e == cudaSuccess && mode == kSweepDiag)
+        e = launch_diag_reduce(a.dpart, grid, a.rec, a.step, false, s);
+    return e;
 }
 
 template <typename real>
 cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim3 grid,
                         dim3 block, cudaStream_t s) {
     init_kernel<real><<<grid, block, 0, s>>>(a, amp, seed);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_diag_reduce(a.dpart, grid, a.rec, 0, true, s);
+    return e;
 }
 
 template <typename real>
