@@ -52,8 +52,8 @@ struct lbm_s {
     dim3 block, grid;
     // scratch: reduction partials, tickets, record; allocated once
     void *scratch = nullptr;
-    double *qpart = nullptr, *dpart = nullptr;
-    unsigned *counters = nullptr;
+    double *qpart = nullptr, *dpart = nullptr, *dpart2 = nullptr;
+    unsigned *counters = nullptr;  // [0]: heated-wall ticket, [1]: diagnostics-fold ticket
     DevRecord *rec = nullptr;
     int nq = 0;
     // FP64 staging for field and population read-back / write (18 x nx*ny
@@ -154,6 +154,8 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.qcount = h->counters;
     a.nq = h->nq;
     a.dpart = h->dpart;
+    a.dpart2 = h->dpart2;
+    a.dticket = h->counters + 1;
     a.rec = h->rec;
     a.step = h->step;
     return a;
@@ -322,13 +324,15 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
         }
     }
     // reduction scratch, carved from one allocation (each piece 256 B aligned):
-    // counter | record | heated-wall partials | per-block diagnostics partials.
+    // counters | record | heated-wall partials | per-block diagnostics partials |
+    // fold-kernel partials.
     // Sized for the largest grid any rows setting gives (one row per block).
     const size_t nblk = (size_t)h->ntx * (size_t)ny;
     const size_t nqmax = (size_t)(h->ntx > ny ? h->ntx : ny);
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t nred = (nblk + 1023) / 1024;
     const size_t o_rec = 256, o_q = o_rec + up(sizeof(DevRecord)), o_d = o_q + up(nqmax * 8),
-                 bytes = o_d + up(nblk * 32);
+                 o_d2 = o_d + up(nblk * 32), bytes = o_d2 + up(nred * 32);
     h->scratch = dev_alloc(h, bytes);
     if (!h->scratch) {
         lbm_destroy(h);
@@ -339,6 +343,7 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     h->rec = reinterpret_cast<DevRecord *>(s + o_rec);
     h->qpart = reinterpret_cast<double *>(s + o_q);
     h->dpart = reinterpret_cast<double *>(s + o_d);
+    h->dpart2 = reinterpret_cast<double *>(s + o_d2);
     e = cudaMemsetAsync(h->scratch, 0, bytes, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -372,7 +377,7 @@ int lbm_set_params(lbm_handle h, const lbm_params *p) {
     h->cur = 0;
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned), h->stream));
     rc = h->precision == LBM_FP64 ? enqueue_init<double>(h) : enqueue_init<float>(h);
     if (rc != LBM_OK) return rc;
     h->params_set = true;

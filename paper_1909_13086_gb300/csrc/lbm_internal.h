@@ -65,8 +65,10 @@ struct SweepArgs {
     unsigned *qcount;      // ticket counter, reset to 0 by the last block
     int nq;                // number of wall-adjacent blocks
     // diagnostics (kSweepDiag, init): 4 partials per block, folded into the
-    // record by a one-block kernel launched right after on the same stream
+    // record by a fold kernel launched right after on the same stream
     double *dpart;
+    double *dpart2;        // fold kernel: 4 partials per fold block
+    unsigned *dticket;     // fold kernel: ticket counter, reset by its last block
     DevRecord *rec;
     long long step;        // step index the launch produces
     // field outputs (kFields), nx*ny doubles each, row-major; NULL = skip

@@ -283,25 +283,53 @@ __device__ __forceinline__ void diag_partial(double (&v)[4], double *dpart, doub
     }
 }
 
-// One block of kReduceThreads threads: thread t folds partials t, t + T, ...
-// in order, then a fixed tree across the block.
+// Fold of the per-block partials in two levels: block r of the fold kernel
+// folds partials [r T, (r + 1) T) (one load per thread, fixed tree) into a
+// level-2 partial; the last of those blocks to take a ticket folds the level-2
+// partials and writes the record.  The order is fixed, so the record is
+// bitwise reproducible for a given launch shape.
 constexpr int kReduceThreads = 1024;
-static __global__ void __launch_bounds__(kReduceThreads)
-    diag_reduce_kernel(const double *dpart, unsigned nblk, DevRecord *rec, double step, int init) {
-    __shared__ double sh[32 * 4];
+
+__device__ __forceinline__ void fold4(double (&acc)[4], double *sh) {
     const int kind[4] = {0, 0, 1, 1};
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const double2 s01 = reinterpret_cast<const double2 *>(dpart)[2 * (size_t)b];
-        const double2 s23 = reinterpret_cast<const double2 *>(dpart)[2 * (size_t)b + 1];
-        acc[0] += s01.x;
-        acc[1] += s01.y;
-        acc[2] = fmax(acc[2], s23.x);
-        acc[3] = fmax(acc[3], s23.y);
-    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
     block_fold<4>(acc, kind, sh);
+}
+
+__device__ __forceinline__ void load4(double (&acc)[4], const double *part, unsigned idx, bool ok) {
+    if (ok) {
+        const double2 s01 = __ldcg(reinterpret_cast<const double2 *>(part) + 2 * (size_t)idx);
+        const double2 s23 = __ldcg(reinterpret_cast<const double2 *>(part) + 2 * (size_t)idx + 1);
+        acc[0] = s01.x;
+        acc[1] = s01.y;
+        acc[2] = s23.x;
+        acc[3] = s23.y;
+    } else {
+        acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+    }
+}
+
+static __global__ void __launch_bounds__(kReduceThreads)
+    diag_reduce_kernel(const double *dpart, unsigned nblk, double *part2, unsigned *ticket,
+                       DevRecord *rec, double step, int init) {
+    __shared__ double sh[32 * 4];
+    __shared__ bool last;
+    double acc[4];
+    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    load4(acc, dpart, idx, idx < nblk);
+    fold4(acc, sh);
+    if (threadIdx.x == 0) {
+        reinterpret_cast<double2 *>(part2)[2 * blockIdx.x] = make_double2(acc[0], acc[1]);
+        reinterpret_cast<double2 *>(part2)[2 * blockIdx.x + 1] = make_double2(acc[2], acc[3]);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    load4(acc, part2, threadIdx.x, threadIdx.x < gridDim.x);
+    fold4(acc, sh);
     if (threadIdx.x == 0) {
         rec->step = step;
         rec->melt_sum = acc[0];
@@ -313,6 +341,7 @@ static __global__ void __launch_bounds__(kReduceThreads)
             rec->Q_last = 0.0;
             rec->Q_cum = 0.0;
         }
+        *ticket = 0u;
     }
 }
 
@@ -329,7 +358,10 @@ __device__ __forceinline__ void prefetch_tile_row_l2(const real *p) {
 
 // ---- the sweep ----
 template <typename real, int PROB, bool FLOW, int MODE>
-__global__ void __launch_bounds__(kTW) lattice_kernel(const SweepArgs<real> a) {
+// FP32: at least 8 blocks of 128 threads per SM (registers capped at 64, the
+// occupancy the memory pipeline needs); FP64 is ALU-bound and keeps its registers.
+__global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
+    lattice_kernel(const SweepArgs<real> a) {
     __shared__ double sh[32 * 4];
     const int lx = threadIdx.x;
     const int x = blockIdx.x * kTW + lx;
@@ -540,10 +572,13 @@ static cudaError_t launch_mode(const SweepArgs<real> &a, int mode, dim3 grid, di
     return cudaGetLastError();
 }
 
-static cudaError_t launch_diag_reduce(const double *dpart, dim3 grid, DevRecord *rec,
-                                      long long step, bool init, cudaStream_t s) {
-    diag_reduce_kernel<<<1, kReduceThreads, 0, s>>>(dpart, grid.x * grid.y, rec, (double)step,
-                                                    init ? 1 : 0);
+template <typename real>
+static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, long long step, bool init,
+                                      cudaStream_t s) {
+    const unsigned nblk = grid.x * grid.y;
+    const unsigned nred = (nblk + kReduceThreads - 1) / kReduceThreads;  // <= kReduceThreads
+    diag_reduce_kernel<<<nred, kReduceThreads, 0, s>>>(a.dpart, nblk, a.dpart2, a.dticket, a.rec,
+                                                       (double)step, init ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -558,7 +593,7 @@ cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int
         e = flow ? launch_mode<real, kStefan, true>(a, mode, grid, block, s)
                  : launch_mode<real, kStefan, false>(a, mode, grid, block, s);
     if (e == cudaSuccess && mode == kSweepDiag)
-        e = launch_diag_reduce(a.dpart, grid, a.rec, a.step, false, s);
+        e = launch_diag_reduce(a, grid, a.step, false, s);
     return e;
 }
 
@@ -567,7 +602,7 @@ cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim
                         dim3 block, cudaStream_t s) {
     init_kernel<real><<<grid, block, 0, s>>>(a, amp, seed);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_diag_reduce(a.dpart, grid, a.rec, 0, true, s);
+    if (e == cudaSuccess) e = launch_diag_reduce(a, grid, 0, true, s);
     return e;
 }
 
