@@ -247,10 +247,12 @@ __device__ __forceinline__ T warp_max(T v) {
     return v;
 }
 
-// Sums (kind 0) or maxes (kind 1) NV doubles over the block, one value per
-// warp (lane 0 holds it); result valid in thread 0.  `sh` holds 32*NV doubles.
-template <int NV>
-__device__ __forceinline__ void block_fold(double (&v)[NV], const int (&kind)[NV], double *sh) {
+// Sums (kind 0) or maxes (kind 1) NV values over the block, one value per
+// warp (lane 0 holds it); result valid in thread 0.  `sh` holds 32*NV 8-byte
+// values.
+template <int NV, typename T>
+__device__ __forceinline__ void block_fold(T (&v)[NV], const int (&kind)[NV], void *shv) {
+    T *sh = static_cast<T *>(shv);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
     if (lane == 0) {
@@ -261,25 +263,58 @@ __device__ __forceinline__ void block_fold(double (&v)[NV], const int (&kind)[NV
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double x = (lane < nwarps) ? sh[k * 32 + lane] : 0.0;
+            T x = (lane < nwarps) ? sh[k * 32 + lane] : T(0);
             v[k] = kind[k] ? warp_max(x) : warp_sum(x);
         }
     }
     __syncthreads();
 }
 
+// ---- diagnostics accumulators ----
+// FP64 path: FP64 throughout.  FP32 path: each warp sums its cells in FP32,
+// then the warp partials are encoded as 64-bit fixed point (2^-24 units) and
+// every fold above the warp is an exact integer sum -- order-independent, and
+// on the integer pipes: on GB300 the FP64 rate (~2 FMA/clock/SM) makes FP64
+// shuffle folds cost as much as the sweep itself.  The maximum |u| travels as
+// the bit pattern of a non-negative float (integer order = float order).  The
+// record receives FP64 values decoded once at the end.  Range: totals up to
+// 2^39 (5.5e11) per quantity.
+template <typename real>
+struct DiagAcc {
+    using T = double;
+};
+template <>
+struct DiagAcc<float> {
+    using T = long long;
+};
+constexpr float kFixScale = 16777216.0f;  // 2^24
+__device__ __forceinline__ long long enc_sum(float v) { return __float2ll_rn(v * kFixScale); }
+__device__ __forceinline__ double enc_sum(double v) { return v; }
+__device__ __forceinline__ long long enc_max(float v) { return (long long)__float_as_int(v); }
+__device__ __forceinline__ double enc_max(double v) { return v; }
+__device__ __forceinline__ double dec_sum(long long q) { return (double)q * (1.0 / 16777216.0); }
+__device__ __forceinline__ double dec_sum(double v) { return v; }
+__device__ __forceinline__ double dec_max(long long q) { return (double)__int_as_float((int)q); }
+__device__ __forceinline__ double dec_max(double v) { return v; }
+
 // Per-block diagnostics partials.  A sweep (or the init kernel) writes one
-// record of 4 doubles per block with plain stores -- no fence, no ticket, so a
-// block's lifetime does not grow -- and diag_reduce_kernel, launched right
-// after on the same stream, folds them in block order (deterministic for a
-// given launch shape) into the FP64 record.
-__device__ __forceinline__ void diag_partial(double (&v)[4], double *dpart, double *sh) {
+// record of 4 accumulators per block with plain stores -- no fence, no ticket,
+// so a block's lifetime does not grow -- and diag_reduce_kernel, launched
+// right after on the same stream, folds them into the FP64 record.  Inputs are
+// the thread's sums in the working precision.
+template <typename real>
+__device__ __forceinline__ void diag_partial(real sfl, real sH, real umax2, bool bad, double *dpart,
+                                             double *sh) {
+    using A = typename DiagAcc<real>::T;
+    const real wfl = warp_sum(sfl), wH = warp_sum(sH), wu = warp_max(umax2);
+    const int wbad = __any_sync(0xffffffffu, bad) ? 1 : 0;
+    A v[4] = {enc_sum(wfl), enc_sum(wH), enc_max(sqrt(wu)), A(wbad)};
     const int kind[4] = {0, 0, 1, 1};
-    block_fold<4>(v, kind, sh);
+    block_fold<4, A>(v, kind, sh);
     if (threadIdx.x == 0) {
-        const size_t bid = blockIdx.x + (size_t)blockIdx.y * gridDim.x;
-        reinterpret_cast<double2 *>(dpart)[2 * bid] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2 *>(dpart)[2 * bid + 1] = make_double2(v[2], v[3]);
+        A *d = reinterpret_cast<A *>(dpart) + 4 * (blockIdx.x + (size_t)blockIdx.y * gridDim.x);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = v[k];
     }
 }
 
@@ -287,55 +322,48 @@ __device__ __forceinline__ void diag_partial(double (&v)[4], double *dpart, doub
 // folds partials [r T, (r + 1) T) (one load per thread, fixed tree) into a
 // level-2 partial; the last of those blocks to take a ticket folds the level-2
 // partials and writes the record.  The order is fixed, so the record is
-// bitwise reproducible for a given launch shape.
+// bitwise reproducible (and on the FP32 path exact in fixed point).
 constexpr int kReduceThreads = 1024;
 
-__device__ __forceinline__ void fold4(double (&acc)[4], double *sh) {
-    const int kind[4] = {0, 0, 1, 1};
+template <typename A>
+__device__ __forceinline__ void load4(A (&acc)[4], const A *part, unsigned idx, bool ok) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
-    block_fold<4>(acc, kind, sh);
+    for (int k = 0; k < 4; ++k) acc[k] = ok ? __ldcg(part + 4 * (size_t)idx + k) : A(0);
 }
 
-__device__ __forceinline__ void load4(double (&acc)[4], const double *part, unsigned idx, bool ok) {
-    if (ok) {
-        const double2 s01 = __ldcg(reinterpret_cast<const double2 *>(part) + 2 * (size_t)idx);
-        const double2 s23 = __ldcg(reinterpret_cast<const double2 *>(part) + 2 * (size_t)idx + 1);
-        acc[0] = s01.x;
-        acc[1] = s01.y;
-        acc[2] = s23.x;
-        acc[3] = s23.y;
-    } else {
-        acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
-    }
-}
-
-static __global__ void __launch_bounds__(kReduceThreads)
+template <typename A>
+__global__ void __launch_bounds__(kReduceThreads)
     diag_reduce_kernel(const double *dpart, unsigned nblk, double *part2, unsigned *ticket,
                        DevRecord *rec, double step, int init) {
     __shared__ double sh[32 * 4];
     __shared__ bool last;
-    double acc[4];
+    const int kind[4] = {0, 0, 1, 1};
+    A acc[4];
     const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-    load4(acc, dpart, idx, idx < nblk);
-    fold4(acc, sh);
+    load4(acc, reinterpret_cast<const A *>(dpart), idx, idx < nblk);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
+    block_fold<4, A>(acc, kind, sh);
     if (threadIdx.x == 0) {
-        reinterpret_cast<double2 *>(part2)[2 * blockIdx.x] = make_double2(acc[0], acc[1]);
-        reinterpret_cast<double2 *>(part2)[2 * blockIdx.x + 1] = make_double2(acc[2], acc[3]);
+        A *d = reinterpret_cast<A *>(part2) + 4 * (size_t)blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = acc[k];
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    load4(acc, part2, threadIdx.x, threadIdx.x < gridDim.x);
-    fold4(acc, sh);
+    load4(acc, reinterpret_cast<const A *>(part2), threadIdx.x, threadIdx.x < gridDim.x);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
+    block_fold<4, A>(acc, kind, sh);
     if (threadIdx.x == 0) {
         rec->step = step;
-        rec->melt_sum = acc[0];
-        rec->H_sum = acc[1];
-        rec->max_u = acc[2];
-        rec->nan_flag = acc[3];
+        rec->melt_sum = dec_sum(acc[0]);
+        rec->H_sum = dec_sum(acc[1]);
+        rec->max_u = dec_max(acc[2]);
+        rec->nan_flag = acc[3] != A(0) ? 1.0 : 0.0;
         rec->valid = 1.0;
         if (init) {
             rec->Q_last = 0.0;
@@ -452,11 +480,7 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
 
     // ---- diagnostics: sums within the warp in the working precision (32
     // threads x `rows` cells), then FP64 across warps and blocks ----
-    if (MODE == kSweepDiag) {
-        double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH),
-                       (double)sqrt(warp_max(umax2)), (double)warp_max(bad ? 1 : 0)};
-        diag_partial(v, a.dpart, sh);
-    }
+    if (MODE == kSweepDiag) diag_partial<real>(sfl, sH, umax2, bad, a.dpart, sh);
 }
 
 // SplitMix64 output function (Steele, Lea & Flood 2014; Vigna's public-domain
@@ -501,8 +525,7 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             bad |= !isfinite(H);
         }
     }
-    double v[4] = {(double)warp_sum(sfl), (double)warp_sum(sH), 0.0, (double)warp_max(bad ? 1 : 0)};
-    diag_partial(v, a.dpart, sh);
+    diag_partial<real>(sfl, sH, real(0), bad, a.dpart, sh);
 }
 
 // Fields of the step-0 state (no streaming; u = 0 by definition).
@@ -577,8 +600,8 @@ static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, long 
                                       cudaStream_t s) {
     const unsigned nblk = grid.x * grid.y;
     const unsigned nred = (nblk + kReduceThreads - 1) / kReduceThreads;  // <= kReduceThreads
-    diag_reduce_kernel<<<nred, kReduceThreads, 0, s>>>(a.dpart, nblk, a.dpart2, a.dticket, a.rec,
-                                                       (double)step, init ? 1 : 0);
+    diag_reduce_kernel<typename DiagAcc<real>::T><<<nred, kReduceThreads, 0, s>>>(
+        a.dpart, nblk, a.dpart2, a.dticket, a.rec, (double)step, init ? 1 : 0);
     return cudaGetLastError();
 }
 
