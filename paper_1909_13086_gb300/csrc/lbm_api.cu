@@ -29,6 +29,18 @@ void *g_alloc_ctx = nullptr;
 
 constexpr int kDefaultRows = 1;      // rows walked by each thread of a block (tuned on GB300)
 constexpr int kDefaultPrefetch = 4;  // L2 prefetch distance in rows (tuned on GB300)
+constexpr int kDefaultGraphChunk = 128;  // steps per replayed CUDA graph (0 = direct launches)
+constexpr int kGraphCache = 8;           // cached chunk graphs per handle
+
+// One captured chunk of sweeps: valid for the buffer parity and the position
+// of the diagnostic sweeps (step mod diag_every) it was captured with.
+struct ChunkGraph {
+    bool used = false;
+    int parity = 0;
+    long long key = 0;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long stamp = 0;
+};
 
 }  // namespace
 
@@ -38,6 +50,9 @@ struct lbm_s {
     int ntx = 0;                // column tiles of kTW cells
     int rows = kDefaultRows;    // rows per block
     int prefetch = kDefaultPrefetch;  // L2 prefetch distance in rows (0 = off)
+    int graph_chunk = kDefaultGraphChunk;
+    ChunkGraph graphs[kGraphCache];
+    unsigned long long graph_clock = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *buf[2] = {nullptr, nullptr};  // 18 planes each
@@ -215,22 +230,105 @@ int derive(lbm_s *h, const lbm_params *p, lbm_derived *d) {
     return LBM_OK;
 }
 
+// One sweep (plus the diagnostics fold after a diagnostic sweep), enqueued on
+// the stream; advances the host's view of the state.
+template <typename real>
+int launch_one(lbm_s *h, bool diag) {
+    const long long next = h->step + 1;
+    SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
+    a.step = next;
+    cudaError_t e = launch_lattice<real>(a, h->p.problem, h->p.flow_on != 0, diag ? kSweepDiag : kSweep,
+                                         h->grid, h->block, h->stream);
+    if (e != cudaSuccess) return set_err(h, LBM_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(e));
+    h->cur ^= 1;
+    h->has_prev = true;
+    h->step = next;
+    return LBM_OK;
+}
+
+bool diag_step(const lbm_s *h, long long step) { return h->diag_every > 0 && step % h->diag_every == 0; }
+
+void drop_graphs(lbm_s *h) {
+    for (ChunkGraph &g : h->graphs) {
+        if (g.used && g.exec) cudaGraphExecDestroy(g.exec);
+        g = ChunkGraph();
+    }
+}
+
+// Replays (capturing first if needed) a graph of graph_chunk sweeps.  Kernel
+// arguments are fixed per chunk: the ping-pong pointers depend only on the
+// parity of the starting buffer and the diagnostic sweeps only on the
+// starting step mod diag_every; everything that changes from step to step
+// (step counter, heated-wall sums, tickets) lives in device memory.
+// Returns LBM_OK, or 1 if graphs cannot be used here (caller launches directly).
+template <typename real>
+int replay_chunk(lbm_s *h) {
+    const int G = h->graph_chunk;
+    const long long key = h->diag_every > 0 ? h->step % h->diag_every : -1;
+    ChunkGraph *slot = nullptr;
+    for (ChunkGraph &g : h->graphs)
+        if (g.used && g.parity == h->cur && g.key == key) slot = &g;
+    if (!slot) {
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(h->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone)
+            return 1;  // the caller is capturing this stream itself
+        ChunkGraph *victim = &h->graphs[0];
+        for (ChunkGraph &g : h->graphs) {
+            if (!g.used) { victim = &g; break; }
+            if (g.stamp < victim->stamp) victim = &g;
+        }
+        if (victim->used && victim->exec) cudaGraphExecDestroy(victim->exec);
+        *victim = ChunkGraph();
+        const int cur0 = h->cur;
+        const long long step0 = h->step;
+        const bool prev0 = h->has_prev;
+        CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = LBM_OK;
+        for (int j = 0; j < G && rc == LBM_OK; ++j) rc = launch_one<real>(h, diag_step(h, h->step + 1));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        h->cur = cur0;
+        h->step = step0;
+        h->has_prev = prev0;
+        if (rc != LBM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess)
+            return set_err(h, LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return set_err(h, LBM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        victim->used = true;
+        victim->parity = cur0;
+        victim->key = key;
+        victim->exec = exec;
+        slot = victim;
+    }
+    slot->stamp = ++h->graph_clock;
+    CUDA_TRY(h, cudaGraphLaunch(slot->exec, h->stream));
+    h->cur ^= (G & 1);
+    h->has_prev = true;
+    h->step += G;
+    return LBM_OK;
+}
+
 template <typename real>
 int enqueue_steps(lbm_s *h, long long n) {
-    for (long long k = 0; k < n; ++k) {
-        const bool last = (k == n - 1);
-        const long long next = h->step + 1;
-        const bool diag = last || (h->diag_every > 0 && next % h->diag_every == 0);
-        SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
-        a.step = next;
-        cudaError_t e = launch_lattice<real>(a, h->p.problem, h->p.flow_on != 0,
-                                             diag ? kSweepDiag : kSweep, h->grid, h->block,
-                                             h->stream);
-        if (e != cudaSuccess)
-            return set_err(h, LBM_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(e));
-        h->cur ^= 1;
-        h->has_prev = true;
-        h->step = next;
+    long long left = n;
+    // whole chunks by graph replay; the last sweep (always diagnostic) and the
+    // remainder by direct launches
+    while (h->graph_chunk >= 2 && left > h->graph_chunk) {
+        const int rc = replay_chunk<real>(h);
+        if (rc == 1) break;
+        if (rc != LBM_OK) return rc;
+        left -= h->graph_chunk;
+    }
+    for (; left > 0; --left) {
+        const int rc = launch_one<real>(h, left == 1 || diag_step(h, h->step + 1));
+        if (rc != LBM_OK) return rc;
     }
     return LBM_OK;
 }
@@ -360,6 +458,7 @@ int lbm_set_params(lbm_handle h, const lbm_params *p) {
     lbm_derived d;
     int rc = derive(h, p, &d);
     if (rc != LBM_OK) return rc;
+    drop_graphs(h);
     h->p = *p;
     h->d = d;
     if (p->problem == LBM_CAVITY && p->strip_width > 0.0) {
@@ -402,6 +501,7 @@ int lbm_step(lbm_handle h, long long n) {
 
 int lbm_set_diag_every(lbm_handle h, long long k) {
     if (!h || k < 0) return set_err(h, LBM_ERR_ARG, "bad argument");
+    if (k != h->diag_every) drop_graphs(h);
     h->diag_every = k;
     return LBM_OK;
 }
@@ -489,15 +589,21 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
     h->step = step;
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
+    const double counter = (double)step;
+    CUDA_TRY(h, cudaMemcpyAsync(&h->rec->counter, &counter, sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 
-int lbm_set_launch(lbm_handle h, int rows, int prefetch_rows) {
-    if (!h || rows < 1 || rows > 1024 || prefetch_rows < 0)
-        return set_err(h, LBM_ERR_ARG, "rows must be in [1, 1024] and prefetch_rows >= 0");
+int lbm_set_launch(lbm_handle h, int rows, int prefetch_rows, int graph_chunk) {
+    if (!h || rows < 1 || rows > 1024 || prefetch_rows < 0 || graph_chunk < 0 || graph_chunk > 65536)
+        return set_err(h, LBM_ERR_ARG,
+                       "rows must be in [1, 1024], prefetch_rows >= 0, graph_chunk in [0, 65536]");
+    drop_graphs(h);
     h->rows = rows;
     h->prefetch = prefetch_rows;
+    h->graph_chunk = graph_chunk;
     set_grid(h);
     return LBM_OK;
 }
@@ -506,6 +612,7 @@ int lbm_destroy(lbm_handle h) {
     if (!h) return LBM_OK;
     DeviceGuard g(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
     dev_free(h, h->buf[0]);
     dev_free(h, h->buf[1]);
     dev_free(h, h->scratch);

@@ -41,6 +41,8 @@ struct DevRecord {
     double max_u;     // max |u|
     double nan_flag;  // 1 if a non-finite H or rho was seen
     double valid;     // 1 once the fields of `step` have been reduced
+    double counter;   // steps taken: advanced by every sweep on the device, so
+                      // that replayed CUDA graphs stamp records correctly
 };
 
 // Arguments of every lattice kernel, passed by value.
@@ -70,7 +72,8 @@ struct SweepArgs {
     double *dpart2;        // fold kernel: 4 partials per fold block
     unsigned *dticket;     // fold kernel: ticket counter, reset by its last block
     DevRecord *rec;
-    long long step;        // step index the launch produces
+    long long step;        // step index the launch produces (host bookkeeping only;
+                           // the record takes its step from rec->counter)
     // field outputs (kFields), nx*ny doubles each, row-major; NULL = skip
     double *oH, *oT, *oFL, *oUX, *oUY, *oRHO;
 };

@@ -334,7 +334,7 @@ __device__ __forceinline__ void load4(A (&acc)[4], const A *part, unsigned idx, 
 template <typename A>
 __global__ void __launch_bounds__(kReduceThreads)
     diag_reduce_kernel(const double *dpart, unsigned nblk, double *part2, unsigned *ticket,
-                       DevRecord *rec, double step, int init) {
+                       DevRecord *rec, int init) {
     __shared__ double sh[32 * 4];
     __shared__ bool last;
     const int kind[4] = {0, 0, 1, 1};
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kReduceThreads)
     for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
     block_fold<4, A>(acc, kind, sh);
     if (threadIdx.x == 0) {
-        rec->step = step;
+        rec->step = init ? 0.0 : rec->counter;
         rec->melt_sum = dec_sum(acc[0]);
         rec->H_sum = dec_sum(acc[1]);
         rec->max_u = dec_max(acc[2]);
@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(kReduceThreads)
         if (init) {
             rec->Q_last = 0.0;
             rec->Q_cum = 0.0;
+            rec->counter = 0.0;
         }
         *ticket = 0u;
     }
@@ -400,6 +401,9 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     // now shortens that block's load latency.
     if (a.prefetch > 0 && threadIdx.x == 0 && y0 + a.prefetch < a.ny)
         prefetch_tile_row_l2(a.src + pop_index(blockIdx.x * kTW, y0 + a.prefetch, 0, a.ny));
+    // the device-side step counter (read by the diagnostics fold after this launch)
+    if (MODE != kFields && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0)
+        a.rec->counter += 1.0;
     const bool active = x < a.nx;
     // the warp's 32 columns are clear of both side walls (warp-uniform)
     const int xw = blockIdx.x * kTW + (lx & ~31);
@@ -596,12 +600,11 @@ static cudaError_t launch_mode(const SweepArgs<real> &a, int mode, dim3 grid, di
 }
 
 template <typename real>
-static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, long long step, bool init,
-                                      cudaStream_t s) {
+static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, bool init, cudaStream_t s) {
     const unsigned nblk = grid.x * grid.y;
     const unsigned nred = (nblk + kReduceThreads - 1) / kReduceThreads;  // <= kReduceThreads
     diag_reduce_kernel<typename DiagAcc<real>::T><<<nred, kReduceThreads, 0, s>>>(
-        a.dpart, nblk, a.dpart2, a.dticket, a.rec, (double)step, init ? 1 : 0);
+        a.dpart, nblk, a.dpart2, a.dticket, a.rec, init ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -616,7 +619,7 @@ cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int
         e = flow ? launch_mode<real, kStefan, true>(a, mode, grid, block, s)
                  : launch_mode<real, kStefan, false>(a, mode, grid, block, s);
     if (e == cudaSuccess && mode == kSweepDiag)
-        e = launch_diag_reduce(a, grid, a.step, false, s);
+        e = launch_diag_reduce(a, grid, false, s);
     return e;
 }
 
@@ -625,7 +628,7 @@ cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim
                         dim3 block, cudaStream_t s) {
     init_kernel<real><<<grid, block, 0, s>>>(a, amp, seed);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_diag_reduce(a, grid, 0, true, s);
+    if (e == cudaSuccess) e = launch_diag_reduce(a, grid, true, s);
     return e;
 }
 

@@ -87,7 +87,7 @@ def lib() -> ctypes.CDLL:
     L.lbm_get_derived.argtypes = [H, ctypes.POINTER(lbm_derived)]
     L.lbm_step.argtypes = [H, ctypes.c_longlong]
     L.lbm_set_diag_every.argtypes = [H, ctypes.c_longlong]
-    L.lbm_set_launch.argtypes = [H, ctypes.c_int, ctypes.c_int]
+    L.lbm_set_launch.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.lbm_read_fields.argtypes = [H, ctypes.c_uint] + [_D] * 6
     L.lbm_diagnostics.argtypes = [H, ctypes.POINTER(lbm_diag)]
     L.lbm_read_populations.argtypes = [H, _D, _D, ctypes.POINTER(ctypes.c_longlong)]
@@ -154,8 +154,8 @@ def lbm_set_diag_every(h, k: int) -> None:
     _check(lib().lbm_set_diag_every(h, int(k)), h)
 
 
-def lbm_set_launch(h, rows: int = 1, prefetch: int = 0) -> None:
-    _check(lib().lbm_set_launch(h, int(rows), int(prefetch)), h)
+def lbm_set_launch(h, rows: int = 1, prefetch: int = 4, graph_chunk: int = 128) -> None:
+    _check(lib().lbm_set_launch(h, int(rows), int(prefetch), int(graph_chunk)), h)
 
 
 def lbm_read_fields(h, mask: int, H=None, T=None, fl=None, ux=None, uy=None, rho=None) -> None:

@@ -341,3 +341,40 @@ def test_full_size_budget_and_bounds_fp32(stream):
     assert 0.0 <= d["melt_fraction"] <= 1.0 and d["melt_fraction"] > d0["melt_fraction"]
     assert abs(d["H_total"] - d0["H_total"] - d["Q_cum"]) <= 1e-3 * d["Q_cum"]
     assert d["max_u"] < 0.3
+
+
+# ------------------------------------------------------------ launch paths
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_graph_replay_matches_direct_launches(stream, prec):
+    """lbm_step replays captured chunk graphs; the state, the heated-wall
+    totals and the diagnostics must be bitwise those of one launch per sweep,
+    including diagnostic sweeps inside the chunks and odd chunk lengths."""
+    nx, ny, p = 300, 77, workloads.params(Ra=1e5, strip_center=0.4)
+    out = []
+    for chunk, diag_every in ((0, 0), (128, 0), (0, 50), (32, 50), (7, 3)):
+        lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+        lbm.lbm_set_launch(lat.h, 1, 4, chunk)
+        lbm.lbm_set_diag_every(lat.h, diag_every)
+        lat.step(413)
+        lat.step(290)
+        f, g, step = lat.populations()
+        out.append((f, g, step, lat.diagnostics()))
+    f0, g0, s0, d0 = out[0]
+    for f, g, s, d in out[1:]:
+        assert s == s0 == 703
+        assert np.array_equal(f, f0) and np.array_equal(g, g0)
+        assert d == d0
+
+
+def test_launch_shape_does_not_change_populations(stream):
+    nx, ny, p = 260, 45, workloads.params(Ra=1e5)
+    ref = None
+    for rows, pf in ((1, 0), (1, 4), (3, 2), (8, 64)):
+        lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+        lbm.lbm_set_launch(lat.h, rows, pf, 16)
+        lat.step(120)
+        f, g, _ = lat.populations()
+        if ref is None:
+            ref = (f, g)
+        else:
+            assert np.array_equal(f, ref[0]) and np.array_equal(g, ref[1])
