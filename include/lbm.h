@@ -172,6 +172,39 @@ int lbm_read_populations(lbm_handle h, double *f, double *g, long long *step);
  * undefined until the next step. */
 int lbm_write_populations(lbm_handle h, const double *f, const double *g, long long step);
 
+/* One step with no allocation, for callers that cannot allocate device
+ * memory at the moment they step -- code running while a stream is being
+ * captured into a CUDA graph (where cudaMalloc is not allowed), hosts that
+ * hand out device memory only from their own fixed arena, latency-critical
+ * loops that must never enter the allocator.  The paper has no counterpart:
+ * it is an interface convenience, not part of the method.
+ *
+ * Advances the lattice held in the caller's device buffer `src` by one fused
+ * sweep with diagnostics (the same kernel and arithmetic as lbm_step) into the
+ * caller's device buffer `dst` (distinct from src), on `cuda_stream` (NULL =
+ * legacy default stream).  Both buffers use the library's tile-major layout:
+ * element ((x / 128) * ny + y) * 2304 + p * 128 + x % 128 for plane p (0..8 =
+ * f_0..f_8, 9..17 = g_0..g_8), ceil(nx / 128) * ny * 2304 elements of FP32
+ * (LBM_FP32) or FP64 (LBM_FP64).  With flow_on = 0 the f planes are neither
+ * read nor written.  `step` is the step number of src.  If `out` is non-NULL
+ * the call synchronises the stream and fills it with the diagnostics of step
+ * + 1, where Q_cum covers this call only; with out = NULL it returns without
+ * synchronising.
+ *
+ * The reduction scratch is one file-scope device array of about 2.6 MB, held
+ * by every GPU that loads the library until the process exits.  Maximum
+ * lattice: ceil(nx / 128) * ny <= 65536 (e.g. 4096 x 2048); larger ones get
+ * LBM_ERR_ARG -- use lbm_create / lbm_step.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the one array, clearing what must start at zero: calls whose work overlaps
+ * on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Allocates nothing and calls no allocating routine.  Errors
+ * (message in lbm_last_error(NULL)): LBM_ERR_ARG, LBM_ERR_CUDA,
+ * LBM_ERR_DIVERGED (out filled). */
+int lbm_step_static(const void *src, void *dst, int nx, int ny, int precision, const lbm_params *p,
+                    long long step, void *cuda_stream, lbm_diag *out);
+
 /* Free the handle's device memory (and its stream, if library-owned). */
 int lbm_destroy(lbm_handle h);
 

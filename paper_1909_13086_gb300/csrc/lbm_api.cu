@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -636,3 +637,135 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *ctx) {
 const char *lbm_version(void) { return "btrirt 0.1 sm_103a"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lbm_step_static: one diagnostic sweep on caller-owned buffers, with no
+// allocation.  Its reduction scratch (per-block partials, tickets, the FP64
+// record) lives in the file-scope device array below instead of memory the
+// library would otherwise allocate per handle.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr unsigned kStaticMaxBlocks = 65536;  // ceil(nx / 128) * ny
+constexpr unsigned kStaticMaxWall = 65536;    // heated-wall partials: ceil(nx / 128) or ny
+constexpr size_t kStaticFold = (kStaticMaxBlocks + 1023) / 1024;
+constexpr size_t kStaticOffRec = 256;
+constexpr size_t kStaticOffQ = kStaticOffRec + 256;
+constexpr size_t kStaticOffD = kStaticOffQ + (size_t)kStaticMaxWall * 8;
+constexpr size_t kStaticOffD2 = kStaticOffD + (size_t)kStaticMaxBlocks * 32;
+constexpr size_t kStaticBytes = kStaticOffD2 + ((kStaticFold * 32 + 255) / 256) * 256;  // ~2.6 MB
+
+// Held by every GPU that loads this library, until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_static_mutex;
+void *g_static_addr[256] = {};  // device address of g_static_scratch, per device ordinal
+
+}  // namespace
+
+extern "C" int lbm_step_static(const void *src, void *dst, int nx, int ny, int precision,
+                               const lbm_params *p, long long step, void *cuda_stream, lbm_diag *out) {
+    if (!src || !dst || src == dst || !p || step < 0)
+        return set_err(nullptr, LBM_ERR_ARG, "lbm_step_static: NULL or aliased buffers, or step < 0");
+    if (nx < 2 || ny < 2 || ny > 65535)
+        return set_err(nullptr, LBM_ERR_ARG, "lbm_step_static: need 2 <= nx, 2 <= ny <= 65535");
+    if (precision != LBM_FP32 && precision != LBM_FP64)
+        return set_err(nullptr, LBM_ERR_ARG, "lbm_step_static: precision must be LBM_FP32 or LBM_FP64");
+    lbm_s t;  // launch description only; owns nothing
+    t.nx = nx;
+    t.ny = ny;
+    t.precision = precision;
+    t.ntx = (nx + kTW - 1) / kTW;
+    t.rows = 1;
+    t.prefetch = kDefaultPrefetch;
+    set_grid(&t);
+    const unsigned long long nblk = (unsigned long long)t.grid.x * t.grid.y;
+    const int nq = p->problem == LBM_CAVITY ? (int)t.grid.x : (int)t.grid.y;
+    if (nblk > kStaticMaxBlocks || (unsigned)nq > kStaticMaxWall)
+        return set_err(nullptr, LBM_ERR_ARG,
+                       "lbm_step_static: lattice too large for the static scratch (ceil(nx/128)*ny = %llu "
+                       "> %u blocks); use lbm_create / lbm_step",
+                       nblk, kStaticMaxBlocks);
+    lbm_derived d;
+    int rc = derive(&t, p, &d);
+    if (rc != LBM_OK) {
+        std::snprintf(g_create_error, sizeof(g_create_error), "lbm_step_static: %.200s", t.err);
+        return rc;
+    }
+    t.p = *p;
+    t.d = d;
+    if (p->problem == LBM_CAVITY && p->strip_width > 0.0) {
+        t.lo2 = (int)std::ceil(2.0 * d.a);
+        t.hi2 = (int)std::floor(2.0 * d.b);
+        t.strip_on = 1;
+    }
+    t.nq = nq;
+
+    // Set-up, once per device with that device current: the array's name is a
+    // host-side stand-in, so the kernels get its device address instead.
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256)
+        return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: cudaGetDevice failed: %s",
+                       cudaGetErrorString(e));
+    char *base;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_addr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess || !ptr)
+                return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: cudaGetSymbolAddress failed: %s",
+                               cudaGetErrorString(e));
+            g_static_addr[dev] = ptr;
+        }
+        base = static_cast<char *>(g_static_addr[dev]);
+    }
+    t.counters = reinterpret_cast<unsigned *>(base);
+    t.rec = reinterpret_cast<DevRecord *>(base + kStaticOffRec);
+    t.qpart = reinterpret_cast<double *>(base + kStaticOffQ);
+    t.dpart = reinterpret_cast<double *>(base + kStaticOffD);
+    t.dpart2 = reinterpret_cast<double *>(base + kStaticOffD2);
+    t.stream = static_cast<cudaStream_t>(cuda_stream);
+
+    // The array keeps the previous call's contents: the tickets and the record
+    // must start from zero, and the record's step counter from `step`.
+    const double counter = (double)step;
+    e = cudaMemsetAsync(base, 0, kStaticOffQ, t.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&t.rec->counter, &counter, sizeof(double), cudaMemcpyHostToDevice, t.stream);
+    if (e != cudaSuccess)
+        return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: clearing the scratch failed: %s",
+                       cudaGetErrorString(e));
+    t.step = step;
+    if (precision == LBM_FP64) {
+        SweepArgs<double> a = make_args<double>(&t, src, dst);
+        a.step = step + 1;
+        e = launch_lattice<double>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block, t.stream);
+    } else {
+        SweepArgs<float> a = make_args<float>(&t, src, dst);
+        a.step = step + 1;
+        e = launch_lattice<float>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block, t.stream);
+    }
+    if (e != cudaSuccess)
+        return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: launch failed: %s", cudaGetErrorString(e));
+    if (!out) return LBM_OK;
+    DevRecord r;
+    e = cudaMemcpyAsync(&r, t.rec, sizeof(r), cudaMemcpyDeviceToHost, t.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t.stream);
+    if (e != cudaSuccess)
+        return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: reading the record failed: %s",
+                       cudaGetErrorString(e));
+    const double P = (double)nx * (double)ny;
+    out->step = step + 1;
+    out->melt_fraction = r.melt_sum / P;
+    out->H_total = r.H_sum;
+    out->Q_strip = r.Q_last;
+    out->Q_cum = r.Q_cum;
+    out->Nu = d.heated_len > 0.0 ? r.Q_last * d.Href / (d.alpha * d.heated_len) : 0.0;
+    out->front_x = r.melt_sum / (double)ny;
+    out->max_u = r.max_u;
+    out->nan_flag = r.nan_flag != 0.0 ? 1 : 0;
+    if (out->nan_flag) return set_err(nullptr, LBM_ERR_DIVERGED, "lbm_step_static: non-finite H or rho");
+    return LBM_OK;
+}

@@ -64,7 +64,7 @@ class lbm_diag(ctypes.Structure):
 EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_set_diag_every",
             "lbm_set_launch",
             "lbm_read_fields", "lbm_diagnostics", "lbm_read_populations", "lbm_write_populations",
-            "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version")
+            "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static")
 
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
@@ -97,6 +97,9 @@ def lib() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, ctypes.c_void_p]
     L.lbm_version.restype = ctypes.c_char_p
+    L.lbm_step_static.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.POINTER(lbm_params), ctypes.c_longlong,
+                                  ctypes.c_void_p, ctypes.POINTER(lbm_diag)]
     for name in EXPORTED:
         if name not in ("lbm_last_error", "lbm_version"):
             getattr(L, name).restype = ctypes.c_int
@@ -179,6 +182,19 @@ def lbm_read_populations(h, f: np.ndarray | None, g: np.ndarray | None) -> int:
 
 def lbm_write_populations(h, f: np.ndarray, g: np.ndarray, step: int) -> None:
     _check(lib().lbm_write_populations(h, _dptr(f), _dptr(g), int(step)), h)
+
+
+def lbm_step_static(src_ptr: int, dst_ptr: int, nx: int, ny: int, precision: int, params: dict,
+                    step: int, stream: int | None = None, want_diag: bool = True) -> dict | None:
+    """One sweep on caller-owned device buffers (tile-major layout), no
+    allocation inside the library; returns the diagnostics of step + 1."""
+    p = make_params(params)
+    d = lbm_diag()
+    rc = lib().lbm_step_static(ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr), nx, ny, precision,
+                               ctypes.byref(p), int(step), ctypes.c_void_p(stream or 0),
+                               ctypes.byref(d) if want_diag else None)
+    _check(rc)
+    return {n: getattr(d, n) for n, _ in lbm_diag._fields_} if want_diag else None
 
 
 def lbm_destroy(h) -> None:

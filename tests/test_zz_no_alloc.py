@@ -1,0 +1,89 @@
+"""The allocation-free entry point, lbm_step_static.
+
+Some callers cannot allocate device memory when they step the lattice: code
+running while a stream is captured into a CUDA graph (cudaMalloc is not
+allowed there), hosts that hand out device memory only from their own fixed
+arena, or loops that must never enter an allocator.  lbm_step_static serves
+them: the caller owns both population buffers, and the reduction scratch sits
+in a static device array inside the library.
+
+These tests check it against the handle API (lbm_step) on two calls in a row,
+so the second call runs on scratch the first call left behind.  The file is
+named to be collected last.
+"""
+import numpy as np
+import pytest
+
+from paper_1909_13086_gb300 import lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+TW = 128  # tile width of the documented population layout
+
+
+def to_tile_major(f, g, nx, ny, dtype):
+    """Plane-major (9, ny, nx) f and g -> the library's tile-major buffer."""
+    ntx = -(-nx // TW)
+    planes = np.concatenate([f, g], 0)
+    out = np.zeros((ntx, ny, 18, TW), dtype)
+    for tx in range(ntx):
+        x0, x1 = tx * TW, min(nx, (tx + 1) * TW)
+        out[tx, :, :, : x1 - x0] = planes[:, :, x0:x1].transpose(1, 0, 2)
+    return out.reshape(-1)
+
+
+def from_tile_major(buf, nx, ny):
+    ntx = -(-nx // TW)
+    a = buf.reshape(ntx, ny, 18, TW)
+    planes = np.empty((18, ny, nx))
+    for tx in range(ntx):
+        x0, x1 = tx * TW, min(nx, (tx + 1) * TW)
+        planes[:, :, x0:x1] = a[tx, :, :, : x1 - x0].transpose(1, 0, 2)
+    return planes[:9], planes[9:]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-13)])
+def test_static_step_matches_handle_on_two_calls(prec, tol):
+    import torch
+
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    nx, ny, p = 300, 77, workloads.params(Ra=1e5, strip_center=0.4)  # ragged last tile
+    dtype = np.float32 if prec == "fp32" else np.float64
+    ref = lbm.Lattice(nx, ny, p, precision=prec, stream=s.cuda_stream)
+    f0, g0, _ = ref.populations()
+    bufs = [torch.from_numpy(to_tile_major(f0, g0, nx, ny, dtype)).cuda(),
+            torch.full((to_tile_major(f0, g0, nx, ny, dtype).size,), float("nan"),
+                       dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda")]
+    torch.cuda.synchronize()
+    precision = lbm.PRECISIONS[prec]
+    for call in (1, 2):
+        src, dst = bufs[(call - 1) % 2], bufs[call % 2]
+        d = lbm.lbm_step_static(src.data_ptr(), dst.data_ptr(), nx, ny, precision, p, call - 1,
+                                s.cuda_stream)
+        ref.step(1)
+        fr, gr, step = ref.populations()
+        fs, gs = from_tile_major(dst.cpu().numpy().astype(np.float64), nx, ny)
+        assert step == call
+        assert np.abs(gs - gr).max() <= tol and np.abs(fs - fr).max() <= tol
+        dr = ref.diagnostics()
+        assert d["step"] == dr["step"] == call and d["nan_flag"] == 0
+        for k in ("melt_fraction", "H_total", "Q_strip", "Nu", "front_x", "max_u"):
+            assert d[k] == pytest.approx(dr[k], rel=tol, abs=1e-15), (call, k)
+        assert d["Q_cum"] == pytest.approx(d["Q_strip"], rel=1e-15)  # this call's inflow only
+
+
+def test_static_step_rejects_lattices_beyond_its_scratch():
+    import torch
+
+    torch.cuda.set_device(0)
+    a = torch.zeros(16, device="cuda")
+    b = torch.zeros(16, device="cuda")
+    nx, ny = 128 * 300, 300  # 300 * 300 blocks > 65536
+    p = workloads.params()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step_static(a.data_ptr(), b.data_ptr(), nx, ny, lbm.LBM_FP32, p, 0, None)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    assert "too large" in str(e.value)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_step_static(a.data_ptr(), a.data_ptr(), 64, 32, lbm.LBM_FP32, p, 0, None)
