@@ -1,0 +1,91 @@
+"""Host-side logic of bench.py: multi-rank aggregation (gloo, world size 2, on
+CPU), launch counting, the ncu-traffic lookup and the clock summary."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r "took" 1 + r seconds for (r + 1) * 100 units
+    t, u = bench.aggregate(1.0 + rank, 100.0 * (rank + 1), dist)
+    q.put((rank, t, u))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_is_max_time_and_sum_of_units_over_ranks():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, t, u in res:
+        assert t == 2.0 and u == 300.0
+
+
+def test_single_rank_aggregate_passthrough():
+    assert bench.aggregate(1.5, 42.0, None) == (1.5, 42.0)
+
+
+def test_sweep_launch_count():
+    # 20000 steps after 200 warm-up: a diagnostic sweep every 100 steps (200 of
+    # them, the last step among them) plus one fold kernel each
+    assert bench.sweep_launches(200, 20000) == 20000 + 200
+    # last step not on the cadence: one extra diagnostic sweep
+    assert bench.sweep_launches(0, 150) == 150 + 2
+    assert bench.sweep_launches(3, 5) == 5 + 1
+
+
+def test_profiled_traffic_needs_matching_kernel_hash(tmp_path, monkeypatch):
+    prof = tmp_path / "p.md"
+    prof.write_text(f"kernel_source_sha256: {bench.kernel_source_hash()}\ndram_bytes_per_launch: 1.5e8\n")
+    monkeypatch.setattr(bench, "PROFILE", str(prof))
+    assert bench.profiled_traffic() == 1.5e8
+    prof.write_text("kernel_source_sha256: 0000000000000000\ndram_bytes_per_launch: 1.5e8\n")
+    assert bench.profiled_traffic() is None
+
+
+def test_measured_peak_falls_back(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peak_gbs() == (bench.FALLBACK_HBM_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6784.8}))
+    assert bench.measured_peak_gbs() == (6784.8, "measured")
+
+
+def test_clock_summary_parses_nvidia_smi_csv(tmp_path):
+    cs = bench.ClockSampler(0)
+    cs.path = str(tmp_path / "c.csv")
+    cs.proc = object()  # pretend the sampler ran
+    with open(cs.path, "w") as fh:
+        fh.write("0, 2070, 2070, 176.5, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        fh.write("0, 1980, 2070, 900.1, 0x4, Not Active, Not Active, Not Active, Active\n")
+        fh.write("0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
