@@ -56,8 +56,11 @@ enum {
     LBM_ERR_TIMEOUT = -6   /* reserved: a bounded device wait ran out          */
 };
 
-/* Storage and arithmetic precision of the populations. */
-enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+/* Storage and arithmetic precision of the populations.  LBM_FP16 and LBM_BF16
+ * store the populations in 16 bits -- f_i as its deviation f_i - w_i from the
+ * rest state, g_i as it is (its rest state at T_m = 0 is zero) -- with all
+ * arithmetic in FP32 and the diagnostics reductions as for LBM_FP32. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
 
 /* Problem kind. */
 enum {

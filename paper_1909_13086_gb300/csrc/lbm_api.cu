@@ -5,6 +5,8 @@
 // sweep kernels on the handle's stream.  No torch types cross this boundary:
 // a framework can lend its stream (cuda_stream) and its allocator
 // (lbm_set_allocator).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -148,8 +150,8 @@ double *staging(lbm_s *h) {
 template <typename real>
 SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     SweepArgs<real> a{};
-    a.src = static_cast<const real *>(src);
-    a.dst = static_cast<real *>(dst);
+    a.src = src;
+    a.dst = dst;
     a.nx = h->nx;
     a.ny = h->ny;
     a.ntx = h->ntx;
@@ -233,12 +235,12 @@ int derive(lbm_s *h, const lbm_params *p, lbm_derived *d) {
 
 // One sweep (plus the diagnostics fold after a diagnostic sweep), enqueued on
 // the stream; advances the host's view of the state.
-template <typename real>
+template <typename real, typename S>
 int launch_one(lbm_s *h, bool diag) {
     const long long next = h->step + 1;
     SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
     a.step = next;
-    cudaError_t e = launch_lattice<real>(a, h->p.problem, h->p.flow_on != 0, diag ? kSweepDiag : kSweep,
+    cudaError_t e = launch_lattice<real, S>(a, h->p.problem, h->p.flow_on != 0, diag ? kSweepDiag : kSweep,
                                          h->grid, h->block, h->stream);
     if (e != cudaSuccess) return set_err(h, LBM_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(e));
     h->cur ^= 1;
@@ -262,7 +264,7 @@ void drop_graphs(lbm_s *h) {
 // starting step mod diag_every; everything that changes from step to step
 // (step counter, heated-wall sums, tickets) lives in device memory.
 // Returns LBM_OK, or 1 if graphs cannot be used here (caller launches directly).
-template <typename real>
+template <typename real, typename S>
 int replay_chunk(lbm_s *h) {
     const int G = h->graph_chunk;
     const long long key = h->diag_every > 0 ? h->step % h->diag_every : -1;
@@ -285,7 +287,7 @@ int replay_chunk(lbm_s *h) {
         const bool prev0 = h->has_prev;
         CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         int rc = LBM_OK;
-        for (int j = 0; j < G && rc == LBM_OK; ++j) rc = launch_one<real>(h, diag_step(h, h->step + 1));
+        for (int j = 0; j < G && rc == LBM_OK; ++j) rc = launch_one<real, S>(h, diag_step(h, h->step + 1));
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
         h->cur = cur0;
@@ -316,49 +318,49 @@ int replay_chunk(lbm_s *h) {
     return LBM_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 int enqueue_steps(lbm_s *h, long long n) {
     long long left = n;
     // whole chunks by graph replay; the last sweep (always diagnostic) and the
     // remainder by direct launches
     while (h->graph_chunk >= 2 && left > h->graph_chunk) {
-        const int rc = replay_chunk<real>(h);
+        const int rc = replay_chunk<real, S>(h);
         if (rc == 1) break;
         if (rc != LBM_OK) return rc;
         left -= h->graph_chunk;
     }
     for (; left > 0; --left) {
-        const int rc = launch_one<real>(h, left == 1 || diag_step(h, h->step + 1));
+        const int rc = launch_one<real, S>(h, left == 1 || diag_step(h, h->step + 1));
         if (rc != LBM_OK) return rc;
     }
     return LBM_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 int enqueue_init(lbm_s *h) {
     SweepArgs<real> a = make_args<real>(h, nullptr, h->buf[h->cur]);
-    a.aux = static_cast<real *>(h->buf[h->cur ^ 1]);
+    a.aux = h->buf[h->cur ^ 1];
     a.step = 0;
-    cudaError_t e = launch_init<real>(a, h->p.init_amp, (uint64_t)h->p.seed, h->grid, h->block,
+    cudaError_t e = launch_init<real, S>(a, h->p.init_amp, (uint64_t)h->p.seed, h->grid, h->block,
                                       h->stream);
     if (e != cudaSuccess)
         return set_err(h, LBM_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 int enqueue_fields(lbm_s *h, double *out[6]) {
     cudaError_t e;
     if (h->step == 0 && !h->has_prev) {
         SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], nullptr);
         a.oH = out[0]; a.oT = out[1]; a.oFL = out[2]; a.oUX = out[3]; a.oUY = out[4]; a.oRHO = out[5];
-        e = launch_fields0<real>(a, h->p.flow_on != 0, h->grid, h->block, h->stream);
+        e = launch_fields0<real, S>(a, h->p.flow_on != 0, h->grid, h->block, h->stream);
     } else {
         // Fields of step n are recomputed from the populations of step n-1,
         // which the ping-pong buffer still holds.
         SweepArgs<real> a = make_args<real>(h, h->buf[h->cur ^ 1], nullptr);
         a.oH = out[0]; a.oT = out[1]; a.oFL = out[2]; a.oUX = out[3]; a.oUY = out[4]; a.oRHO = out[5];
-        e = launch_lattice<real>(a, h->p.problem, h->p.flow_on != 0, kFields, h->grid, h->block,
+        e = launch_lattice<real, S>(a, h->p.problem, h->p.flow_on != 0, kFields, h->grid, h->block,
                                  h->stream);
     }
     if (e != cudaSuccess)
@@ -366,13 +368,30 @@ int enqueue_fields(lbm_s *h, double *out[6]) {
     return LBM_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 int repack(lbm_s *h, void *buf, void *buf2, bool to_staging) {
-    cudaError_t e = launch_repack<real>(static_cast<real *>(buf), static_cast<real *>(buf2), h->stage,
-                                       h->nx, h->ny, to_staging, h->stream);
+    cudaError_t e = launch_repack<S>(buf, buf2, h->stage, h->nx, h->ny, to_staging, h->stream);
     if (e != cudaSuccess) return set_err(h, LBM_ERR_CUDA, "repack launch failed: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
+
+// Calls fn(Types<real, S>{}) for the handle's precision: the arithmetic type
+// and the storage type of the populations.
+template <typename R, typename S>
+struct Types {
+    using real = R;
+    using store = S;
+};
+template <typename Fn>
+int by_precision(int precision, Fn &&fn) {
+    switch (precision) {
+        case LBM_FP64: return fn(Types<double, double>{});
+        case LBM_FP16: return fn(Types<float, __half>{});
+        case LBM_BF16: return fn(Types<float, __nv_bfloat16>{});
+        default: return fn(Types<float, float>{});
+    }
+}
+#define BTRIRT_T(t, F) F<typename decltype(t)::real, typename decltype(t)::store>
 
 }  // namespace
 
@@ -385,8 +404,8 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     if (ny > 65535) return set_err(nullptr, LBM_ERR_ARG, "ny must be <= 65535");
     if ((long long)nx * ny > (1ll << 31))
         return set_err(nullptr, LBM_ERR_ARG, "lattice larger than 2^31 cells");
-    if (precision != LBM_FP32 && precision != LBM_FP64)
-        return set_err(nullptr, LBM_ERR_ARG, "precision must be LBM_FP32 or LBM_FP64");
+    if (precision != LBM_FP32 && precision != LBM_FP64 && precision != LBM_FP16 && precision != LBM_BF16)
+        return set_err(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64, LBM_FP32, LBM_FP16 or LBM_BF16");
     lbm_s *h = new (std::nothrow) lbm_s();
     if (!h) return set_err(nullptr, LBM_ERR_OOM, "host allocation failed");
     cudaError_t e = cudaGetDevice(&h->device);
@@ -397,7 +416,7 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     h->nx = nx;
     h->ny = ny;
     h->precision = precision;
-    h->esize = precision == LBM_FP64 ? 8 : 4;
+    h->esize = precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
     h->ntx = (nx + kTW - 1) / kTW;
     set_grid(h);
     h->alloc = g_alloc;
@@ -478,7 +497,7 @@ int lbm_set_params(lbm_handle h, const lbm_params *p) {
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned), h->stream));
-    rc = h->precision == LBM_FP64 ? enqueue_init<double>(h) : enqueue_init<float>(h);
+    rc = by_precision(h->precision, [&](auto t) { return BTRIRT_T(t, enqueue_init)(h); });
     if (rc != LBM_OK) return rc;
     h->params_set = true;
     return LBM_OK;
@@ -497,7 +516,7 @@ int lbm_step(lbm_handle h, long long n) {
     if (!h->params_set) return set_err(h, LBM_ERR_STATE, "parameters not set");
     if (n == 0) return LBM_OK;
     DeviceGuard g(h->device);
-    return h->precision == LBM_FP64 ? enqueue_steps<double>(h, n) : enqueue_steps<float>(h, n);
+    return by_precision(h->precision, [&](auto t) { return BTRIRT_T(t, enqueue_steps)(h, n); });
 }
 
 int lbm_set_diag_every(lbm_handle h, long long k) {
@@ -520,7 +539,7 @@ int lbm_read_fields(lbm_handle h, unsigned mask, double *H, double *T, double *f
     double *host[6] = {H, T, fl, ux, uy, rho};
     double *dev[6];
     for (int k = 0; k < 6; ++k) dev[k] = ((mask >> k) & 1u) && host[k] ? stage + k * P : nullptr;
-    int rc = h->precision == LBM_FP64 ? enqueue_fields<double>(h, dev) : enqueue_fields<float>(h, dev);
+    int rc = by_precision(h->precision, [&](auto t) { return BTRIRT_T(t, enqueue_fields)(h, dev); });
     if (rc != LBM_OK) return rc;
     for (int k = 0; k < 6; ++k)
         if (dev[k])
@@ -559,8 +578,8 @@ int lbm_read_populations(lbm_handle h, double *f, double *g, long long *step) {
     DeviceGuard gd(h->device);
     if (!staging(h)) return set_err(h, LBM_ERR_OOM, "device allocation of the staging failed");
     const size_t half = (size_t)9 * h->nx * h->ny;
-    int rc = h->precision == LBM_FP64 ? repack<double>(h, h->buf[h->cur], nullptr, true)
-                                      : repack<float>(h, h->buf[h->cur], nullptr, true);
+    int rc = by_precision(h->precision,
+                          [&](auto t) { return BTRIRT_T(t, repack)(h, h->buf[h->cur], nullptr, true); });
     if (rc != LBM_OK) return rc;
     if (f)
         CUDA_TRY(h, cudaMemcpyAsync(f, h->stage, half * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -584,8 +603,8 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
     // With the flow off the f planes are never rewritten by a sweep, so both
     // buffers receive them.
     void *other = h->p.flow_on ? nullptr : h->buf[h->cur ^ 1];
-    int rc = h->precision == LBM_FP64 ? repack<double>(h, h->buf[h->cur], other, false)
-                                      : repack<float>(h, h->buf[h->cur], other, false);
+    int rc = by_precision(h->precision,
+                          [&](auto t) { return BTRIRT_T(t, repack)(h, h->buf[h->cur], other, false); });
     if (rc != LBM_OK) return rc;
     h->step = step;
     h->has_prev = false;
@@ -741,11 +760,13 @@ extern "C" int lbm_step_static(const void *src, void *dst, int nx, int ny, int p
     if (precision == LBM_FP64) {
         SweepArgs<double> a = make_args<double>(&t, src, dst);
         a.step = step + 1;
-        e = launch_lattice<double>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block, t.stream);
+        e = launch_lattice<double, double>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block,
+                                           t.stream);
     } else {
         SweepArgs<float> a = make_args<float>(&t, src, dst);
         a.step = step + 1;
-        e = launch_lattice<float>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block, t.stream);
+        e = launch_lattice<float, float>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block,
+                                         t.stream);
     }
     if (e != cudaSuccess)
         return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: launch failed: %s", cudaGetErrorString(e));

@@ -48,9 +48,11 @@ struct DevRecord {
 // Arguments of every lattice kernel, passed by value.
 template <typename real>
 struct SweepArgs {
-    const real *src;       // tile-major populations of the previous step
-    real *dst;             // tile-major populations written by this step
-    real *aux;             // init only: the other buffer, whose f planes are also
+    // Population buffers, tile-major, of the storage type S the launcher was
+    // instantiated with (float, double, __half or __nv_bfloat16).
+    const void *src;       // populations of the previous step
+    void *dst;             // populations written by this step
+    void *aux;             // init only: the other buffer, whose f planes are also
                            // set to w_i (they are never rewritten when flow is off)
     int nx, ny;            // lattice size
     int ntx;               // number of column tiles
@@ -78,21 +80,24 @@ struct SweepArgs {
     double *oH, *oT, *oFL, *oUX, *oUY, *oRHO;
 };
 
-// Launchers (defined in sweep_fp32.cu / sweep_fp64.cu).
-template <typename real>
+// Launchers, instantiated in sweep_fp32.cu / sweep_fp64.cu / sweep_f16.cu for
+// (compute real, storage S) = (float, float), (double, double),
+// (float, __half), (float, __nv_bfloat16).
+template <typename real, typename S>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
                            dim3 grid, dim3 block, cudaStream_t s);
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim3 grid,
                         dim3 block, cudaStream_t s);
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_fields0(const SweepArgs<real> &a, bool flow, dim3 grid, dim3 block,
                            cudaStream_t s);
 // Tile-major buffer <-> plane-major FP64 staging (18 planes of nx*ny, f then g).
 // to_staging = true packs buf into stage; false unpacks stage into buf (and,
-// if buf2 is non-NULL, the f planes into buf2 as well).
-template <typename real>
-cudaError_t launch_repack(real *buf, real *buf2, double *stage, int nx, int ny, bool to_staging,
+// if buf2 is non-NULL, the f planes into buf2 as well).  Values in the staging
+// are the populations themselves, whatever the storage encoding.
+template <typename S>
+cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, bool to_staging,
                           cudaStream_t s);
 
 }  // namespace btrirt

@@ -28,9 +28,13 @@
 // about 4 flops per population instead of re-forming every n_i.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "lbm_internal.h"
 
@@ -49,6 +53,43 @@ __host__ __device__ constexpr int opp_of(int i) {
 template <typename real>
 __device__ __forceinline__ real w_of(int i) {
     return i == 0 ? real(4) / real(9) : (i <= 4 ? real(1) / real(9) : real(1) / real(36));
+}
+
+// ---- storage encodings ----
+// FP32 / FP64: populations as they are.  FP16 / BF16 (arithmetic in FP32):
+// f_i is stored as its deviation f_i - w_i from the rest state (rho = 1, u = 0),
+// g_i as it is -- its rest state (solid at T_m = 0) is zero.  Rounding to the
+// 16-bit format is round-to-nearest-even.
+template <typename S>
+struct Store;
+template <>
+struct Store<float> {
+    static constexpr bool kDev = false;
+    __device__ static float ld(const float *p) { return __ldg(p); }
+    __device__ static void st(float *p, float v) { *p = v; }
+};
+template <>
+struct Store<double> {
+    static constexpr bool kDev = false;
+    __device__ static double ld(const double *p) { return __ldg(p); }
+    __device__ static void st(double *p, double v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+    static constexpr bool kDev = true;
+    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    static constexpr bool kDev = true;
+    __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+// Offset added to a stored f value (plane i) to recover f_i.
+template <typename real, typename S>
+__device__ __forceinline__ real f_ofs(int i) {
+    return Store<S>::kDev ? w_of<real>(i) : real(0);
 }
 
 // ---- H -> (T, f_l): H_s = C_p T_m = 0, H_l = H_s + L.
@@ -179,31 +220,37 @@ __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, rea
 // Interior cell: no wall in reach.  b points at (x, y, plane 0); bL / bR equal
 // b except at the tile's first / last column, where they are shifted so that
 // bL[-1] / bR[+1] land in the neighbouring tile.
-template <typename real, bool FLOW>
-__device__ __forceinline__ void pull_fast(const real *__restrict__ b, const real *__restrict__ bL,
-                                          const real *__restrict__ bR, real f[9], real g[9]) {
+template <typename real, typename S, bool FLOW>
+__device__ __forceinline__ void pull_fast(const S *__restrict__ b, const S *__restrict__ bL,
+                                          const S *__restrict__ bR, real f[9], real g[9]) {
     constexpr int R = kRS, W = kTW;
-#define BTRIRT_PULL(P, arr)                                          \
-    arr[0] = __ldg(b + (P + 0) * W);                                 \
-    arr[1] = __ldg(bL + (P + 1) * W - 1);                            \
-    arr[2] = __ldg(b + (P + 2) * W - R);                             \
-    arr[3] = __ldg(bR + (P + 3) * W + 1);                            \
-    arr[4] = __ldg(b + (P + 4) * W + R);                             \
-    arr[5] = __ldg(bL + (P + 5) * W - R - 1);                        \
-    arr[6] = __ldg(bR + (P + 6) * W - R + 1);                        \
-    arr[7] = __ldg(bR + (P + 7) * W + R + 1);                        \
-    arr[8] = __ldg(bL + (P + 8) * W + R - 1);
-    BTRIRT_PULL(9, g)
+    using St = Store<S>;
+#define BTRIRT_PULL(P, arr, OFS)                                         \
+    arr[0] = St::ld(b + (P + 0) * W) + OFS(0);                           \
+    arr[1] = St::ld(bL + (P + 1) * W - 1) + OFS(1);                      \
+    arr[2] = St::ld(b + (P + 2) * W - R) + OFS(2);                       \
+    arr[3] = St::ld(bR + (P + 3) * W + 1) + OFS(3);                      \
+    arr[4] = St::ld(b + (P + 4) * W + R) + OFS(4);                       \
+    arr[5] = St::ld(bL + (P + 5) * W - R - 1) + OFS(5);                  \
+    arr[6] = St::ld(bR + (P + 6) * W - R + 1) + OFS(6);                  \
+    arr[7] = St::ld(bR + (P + 7) * W + R + 1) + OFS(7);                  \
+    arr[8] = St::ld(bL + (P + 8) * W + R - 1) + OFS(8);
+#define BTRIRT_NOOFS(i) real(0)
+#define BTRIRT_FOFS(i) f_ofs<real, S>(i)
+    BTRIRT_PULL(9, g, BTRIRT_NOOFS)
     if (FLOW) {
-        BTRIRT_PULL(0, f)
+        BTRIRT_PULL(0, f, BTRIRT_FOFS)
     }
 #undef BTRIRT_PULL
+#undef BTRIRT_NOOFS
+#undef BTRIRT_FOFS
 }
 
 // Any cell: explicit source test per direction and the wall rules.
-template <typename real, int PROB, bool FLOW>
+template <typename real, typename S, int PROB, bool FLOW>
 __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y, real f[9],
                                          real g[9], real &q) {
+    const S *src = static_cast<const S *>(a.src);
     const long long self = pop_index(x, y, 0, a.ny);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -213,8 +260,8 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
         const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
         const long long cell = in ? pop_index(sx, sy, 0, a.ny) : self;
         const int pl = in ? i : opp_of(i);
-        real gv = __ldg(a.src + cell + (9 + pl) * kTW);
-        if (FLOW) f[i] = __ldg(a.src + cell + pl * kTW);
+        real gv = Store<S>::ld(src + cell + (9 + pl) * kTW);
+        if (FLOW) f[i] = Store<S>::ld(src + cell + pl * kTW) + f_ofs<real, S>(pl);
         if (!in) {
             bool heated;
             if (PROB == kStefan) {
@@ -376,21 +423,23 @@ __global__ void __launch_bounds__(kReduceThreads)
 
 // Bulk prefetch of one contiguous tile row (all 18 planes, kRS values) into
 // L2: a single TMA-unit request, no registers or shared memory involved.  The
-// address is 16 B aligned (tile rows are kRS * sizeof(real) bytes apart from a
+// address is 16 B aligned (tile rows are kRS * sizeof(S) bytes apart from a
 // 256 B aligned base) and the size a multiple of 16.
-template <typename real>
-__device__ __forceinline__ void prefetch_tile_row_l2(const real *p) {
+template <typename S>
+__device__ __forceinline__ void prefetch_tile_row_l2(const S *p) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p),
-                 "r"((unsigned)(kRS * sizeof(real)))
+                 "r"((unsigned)(kRS * sizeof(S)))
                  : "memory");
 }
 
 // ---- the sweep ----
-template <typename real, int PROB, bool FLOW, int MODE>
-// FP32: at least 8 blocks of 128 threads per SM (registers capped at 64, the
-// occupancy the memory pipeline needs); FP64 is ALU-bound and keeps its registers.
+template <typename real, typename S, int PROB, bool FLOW, int MODE>
+// FP32 arithmetic: at least 8 blocks of 128 threads per SM (registers capped at
+// 64, the occupancy the memory pipeline needs); FP64 is ALU-bound and keeps its
+// registers.
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     lattice_kernel(const SweepArgs<real> a) {
+    const S *src = static_cast<const S *>(a.src);
     __shared__ double sh[32 * 4];
     const int lx = threadIdx.x;
     const int x = blockIdx.x * kTW + lx;
@@ -400,7 +449,7 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     // ahead belongs to a block that starts a little later: fetching it into L2
     // now shortens that block's load latency.
     if (a.prefetch > 0 && threadIdx.x == 0 && y0 + a.prefetch < a.ny)
-        prefetch_tile_row_l2(a.src + pop_index(blockIdx.x * kTW, y0 + a.prefetch, 0, a.ny));
+        prefetch_tile_row_l2(src + pop_index(blockIdx.x * kTW, y0 + a.prefetch, 0, a.ny));
     // the device-side step counter (read by the diagnostics fold after this launch)
     if (MODE != kFields && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0)
         a.rec->counter += 1.0;
@@ -423,9 +472,9 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
         if (!active) continue;
         real f[9], g[9];
         if (fastcol && y >= 1 && y <= a.ny - 2) {
-            pull_fast<real, FLOW>(a.src + i0, a.src + iL, a.src + iR, f, g);
+            pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
         } else {
-            pull_any<real, PROB, FLOW>(a, x, y, f, g, q);
+            pull_any<real, S, PROB, FLOW>(a, x, y, f, g, q);
         }
         if (MODE == kFields) {
             const Macro<real> m = cell_update<real, FLOW, false>(a, f, g);
@@ -439,11 +488,11 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
             continue;
         }
         const Macro<real> m = cell_update<real, FLOW, true>(a, f, g);
-        real *d = a.dst + pop_index(x, y, 0, a.ny);
+        S *d = static_cast<S *>(a.dst) + pop_index(x, y, 0, a.ny);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            d[(9 + i) * kTW] = g[i];
-            if (FLOW) d[i * kTW] = f[i];
+            Store<S>::st(d + (9 + i) * kTW, g[i]);
+            if (FLOW) Store<S>::st(d + i * kTW, f[i] - f_ofs<real, S>(i));
         }
         if (MODE == kSweepDiag) {
             sfl += m.fl;
@@ -499,9 +548,11 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t v) {
 // Step-0 state: H0 = amp (2r - 1) (solid at T_m = 0 with a seeded perturbation
 // of T), f_i = w_i, g_i = g_eq(H0, T(H0), u = 0) (Eq. 4); reduces the step-0
 // diagnostics.
-template <typename real>
+template <typename real, typename S>
 __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, double amp,
                                                    uint64_t seed) {
+    S *dst = static_cast<S *>(a.dst);
+    S *aux = static_cast<S *>(a.aux);
     __shared__ double sh[32 * 4];
     const int x = blockIdx.x * kTW + threadIdx.x;
     const int y0 = blockIdx.y * a.rows;
@@ -516,13 +567,14 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             real T, fl;
             invert(H, a.Lh, T, fl);
             const long long c = pop_index(x, y, 0, a.ny);
-            a.dst[c + 9 * kTW] = H - T + w_of<real>(0) * T;
+            Store<S>::st(dst + c + 9 * kTW, H - T + w_of<real>(0) * T);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) a.dst[c + (9 + i) * kTW] = w_of<real>(i) * T;
+            for (int i = 1; i < 9; ++i) Store<S>::st(dst + c + (9 + i) * kTW, w_of<real>(i) * T);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                a.dst[c + i * kTW] = w_of<real>(i);
-                if (a.aux) a.aux[c + i * kTW] = w_of<real>(i);
+                const real fi = w_of<real>(i) - f_ofs<real, S>(i);
+                Store<S>::st(dst + c + i * kTW, fi);
+                if (aux) Store<S>::st(aux + c + i * kTW, fi);
             }
             sfl += fl;
             sH += H;
@@ -533,8 +585,9 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
 }
 
 // Fields of the step-0 state (no streaming; u = 0 by definition).
-template <typename real, bool FLOW>
+template <typename real, typename S, bool FLOW>
 __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
+    const S *src = static_cast<const S *>(a.src);
     const int x = blockIdx.x * kTW + threadIdx.x;
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
@@ -543,12 +596,12 @@ __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
         const long long c = pop_index(x, y, 0, a.ny);
         real g[9], H, rho = real(1);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = a.src[c + (9 + i) * kTW];
+        for (int i = 0; i < 9; ++i) g[i] = Store<S>::ld(src + c + (9 + i) * kTW);
         H = sum9(g);
         if (FLOW) {
             real f[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = a.src[c + i * kTW];
+            for (int i = 0; i < 9; ++i) f[i] = Store<S>::ld(src + c + i * kTW) + f_ofs<real, S>(i);
             rho = sum9(f);
         }
         real T, fl;
@@ -564,9 +617,11 @@ __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
 }
 
 // Tile-major <-> plane-major FP64 staging, one thread per cell.
-template <typename real>
-__global__ void repack_kernel(real *buf, real *buf2, double *stage, int nx, int ny,
+template <typename S>
+__global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, int ny,
                               bool to_staging) {
+    using real = typename std::conditional<sizeof(S) == 8, double, float>::type;
+    S *buf = static_cast<S *>(bufv), *buf2 = static_cast<S *>(buf2v);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= nx) return;
@@ -574,26 +629,27 @@ __global__ void repack_kernel(real *buf, real *buf2, double *stage, int nx, int 
     const long long P = (long long)nx * ny, o = (long long)y * nx + x;
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
+        const real ofs = p < 9 ? f_ofs<real, S>(p) : real(0);
         if (to_staging) {
-            stage[p * P + o] = (double)buf[c + p * kTW];
+            stage[p * P + o] = (double)(Store<S>::ld(buf + c + p * kTW) + ofs);
         } else {
-            const real v = (real)stage[p * P + o];
-            buf[c + p * kTW] = v;
-            if (buf2 && p < 9) buf2[c + p * kTW] = v;
+            const real v = (real)stage[p * P + o] - ofs;
+            Store<S>::st(buf + c + p * kTW, v);
+            if (buf2 && p < 9) Store<S>::st(buf2 + c + p * kTW, v);
         }
     }
 }
 
-// ---- launch dispatch (instantiated per precision in sweep_fp32/64.cu) ----
-template <typename real, int PROB, bool FLOW>
+// ---- launch dispatch (instantiated per storage type in sweep_*.cu) ----
+template <typename real, typename S, int PROB, bool FLOW>
 static cudaError_t launch_mode(const SweepArgs<real> &a, int mode, dim3 grid, dim3 block,
                                cudaStream_t s) {
     switch (mode) {
-        case kSweep: lattice_kernel<real, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(a); break;
+        case kSweep: lattice_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(a); break;
         case kSweepDiag:
-            lattice_kernel<real, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(a);
+            lattice_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(a);
             break;
-        case kFields: lattice_kernel<real, PROB, FLOW, kFields><<<grid, block, 0, s>>>(a); break;
+        case kFields: lattice_kernel<real, S, PROB, FLOW, kFields><<<grid, block, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -608,46 +664,55 @@ static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, bool 
     return cudaGetLastError();
 }
 
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
                            dim3 grid, dim3 block, cudaStream_t s) {
     cudaError_t e;
     if (problem == kCavity)
-        e = flow ? launch_mode<real, kCavity, true>(a, mode, grid, block, s)
-                 : launch_mode<real, kCavity, false>(a, mode, grid, block, s);
+        e = flow ? launch_mode<real, S, kCavity, true>(a, mode, grid, block, s)
+                 : launch_mode<real, S, kCavity, false>(a, mode, grid, block, s);
     else
-        e = flow ? launch_mode<real, kStefan, true>(a, mode, grid, block, s)
-                 : launch_mode<real, kStefan, false>(a, mode, grid, block, s);
-    if (e == cudaSuccess && mode == kSweepDiag)
-        e = launch_diag_reduce(a, grid, false, s);
+        e = flow ? launch_mode<real, S, kStefan, true>(a, mode, grid, block, s)
+                 : launch_mode<real, S, kStefan, false>(a, mode, grid, block, s);
+    if (e == cudaSuccess && mode == kSweepDiag) e = launch_diag_reduce(a, grid, false, s);
     return e;
 }
 
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim3 grid,
                         dim3 block, cudaStream_t s) {
-    init_kernel<real><<<grid, block, 0, s>>>(a, amp, seed);
+    init_kernel<real, S><<<grid, block, 0, s>>>(a, amp, seed);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_diag_reduce(a, grid, true, s);
     return e;
 }
 
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_fields0(const SweepArgs<real> &a, bool flow, dim3 grid, dim3 block,
                            cudaStream_t s) {
     if (flow)
-        fields0_kernel<real, true><<<grid, block, 0, s>>>(a);
+        fields0_kernel<real, S, true><<<grid, block, 0, s>>>(a);
     else
-        fields0_kernel<real, false><<<grid, block, 0, s>>>(a);
+        fields0_kernel<real, S, false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename real>
-cudaError_t launch_repack(real *buf, real *buf2, double *stage, int nx, int ny, bool to_staging,
+template <typename S>
+cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, bool to_staging,
                           cudaStream_t s) {
     dim3 block(256), grid((nx + 255) / 256, ny);
-    repack_kernel<real><<<grid, block, 0, s>>>(buf, buf2, stage, nx, ny, to_staging);
+    repack_kernel<S><<<grid, block, 0, s>>>(buf, buf2, stage, nx, ny, to_staging);
     return cudaGetLastError();
 }
+
+// Explicit instantiation of every launcher for one (compute, storage) pair.
+#define BTRIRT_INSTANTIATE(REAL, S)                                                             \
+    template cudaError_t launch_lattice<REAL, S>(const SweepArgs<REAL> &, int, bool, int, dim3,  \
+                                                 dim3, cudaStream_t);                            \
+    template cudaError_t launch_init<REAL, S>(const SweepArgs<REAL> &, double, uint64_t, dim3,   \
+                                              dim3, cudaStream_t);                               \
+    template cudaError_t launch_fields0<REAL, S>(const SweepArgs<REAL> &, bool, dim3, dim3,      \
+                                                 cudaStream_t);                                  \
+    template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t);
 
 }  // namespace btrirt

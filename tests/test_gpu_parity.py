@@ -378,3 +378,72 @@ def test_launch_shape_does_not_change_populations(stream):
             ref = (f, g)
         else:
             assert np.array_equal(f, ref[0]) and np.array_equal(g, ref[1])
+
+
+# ------------------------------------------------------------ 16-bit storage
+def _w():
+    return np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def _bf16(x32):
+    """Round float32 values to bfloat16 (nearest, ties to even), back as float32."""
+    b = np.ascontiguousarray(x32, np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _encode(f, g, prec):
+    """What the 16-bit storage holds, decoded: f_i as w_i + q(f_i - w_i), g_i as
+    q(g_i), with the FP32 arithmetic the device uses."""
+    q = (lambda a: a.astype(np.float16).astype(np.float32)) if prec == "fp16" else _bf16
+    w = _w().astype(np.float32)[:, None, None]
+    f32, g32 = f.astype(np.float32), g.astype(np.float32)
+    return ((q(f32 - w) + w).astype(np.float64), q(g32).astype(np.float64))
+
+
+def _ulp16(a, prec):
+    """One unit in the last place of the 16-bit format at |a| (>= its min normal)."""
+    mant = 10 if prec == "fp16" else 7
+    tiny = 2.0 ** -14 if prec == "fp16" else 2.0 ** -126
+    return 2.0 ** (np.floor(np.log2(np.maximum(np.abs(a), tiny))) - mant)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_16bit_single_step_matches_oracle_to_one_ulp(orc, stream, prec):
+    """From a state the 16-bit storage holds exactly, one step on the GPU (FP32
+    arithmetic, result rounded to 16 bits) equals the FP64 oracle's step rounded
+    the same way, to one unit in the last place of the 16-bit format."""
+    nx, ny, p = 70, 33, workloads.params(Ra=1e6, strip_center=0.4, strip_width=0.35)
+    f, g = workloads.random_populations(nx, ny, seed=12)
+    f, g = _encode(f, g, prec)
+    ref = orc.Oracle(nx, ny, **p)
+    ref.set_populations(f, g, step=3)
+    ref.step(1)
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    lat.set_populations(f, g, step=3)
+    f_in, g_in, _ = lat.populations()
+    assert np.array_equal(f_in, f) and np.array_equal(g_in, g)  # lossless round trip
+    lat.step(1)
+    fo, go, _ = lat.populations()
+    fr, gr = ref.populations()
+    w = _w()[:, None, None]
+    assert np.all(np.abs(go - gr) <= _ulp16(gr, prec) + 1e-6 * np.abs(gr) + 1e-30)
+    assert np.all(np.abs((fo - w) - (fr - w)) <= _ulp16(fr - w, prec) + 1e-6 * np.abs(fr) + 1e-30)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_16bit_cavity_tracks_fp64(stream, prec):
+    """64 x 32 cavity, 2000 steps: the 16-bit runs stay bounded and close to the
+    FP64 run (melt fraction within 2e-3, enthalpy budget within 1e-3)."""
+    nx, ny, p = workloads.cavity_64x32()
+    runs = {}
+    for pr in ("fp64", prec):
+        lat = lbm.Lattice(nx, ny, p, precision=pr, stream=stream)
+        h0 = lat.diagnostics()["H_total"]
+        lat.step(2000)
+        runs[pr] = (lat.diagnostics(), h0)
+    d, h0 = runs[prec]
+    d64, _ = runs["fp64"]
+    assert d["nan_flag"] == 0
+    assert abs(d["melt_fraction"] - d64["melt_fraction"]) <= 2e-3
+    assert abs(d["H_total"] - h0 - d["Q_cum"]) <= 1e-3 * d["Q_cum"] + 1e-2
