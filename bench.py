@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NX, NY = 2048, 1024
-BYTES_PER_LUP = {"fp32": 144, "fp64": 288, "fp16": 72, "bf16": 72}  # 18 read + 18 written
+BYTES_PER_LUP = {"fp32": 144, "fp64": 288, "fp16": 72, "bf16": 72, "fp16sr": 72, "bf16sr": 72}  # 18 read + 18 written
 DIAG_EVERY = 100
 METRIC = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
@@ -337,7 +337,8 @@ def run_ours(args) -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)",
-                  "bf16": "f32 (bf16 storage)"}[prec], "data": "synthetic",
+                  "bf16": "f32 (bf16 storage)", "fp16sr": "f32 (f16 storage, stochastic rounding)",
+                  "bf16sr": "f32 (bf16 storage, stochastic rounding)"}[prec], "data": "synthetic",
         "config": workload_config(prec),
         "roofline": roofline,
         "e2e": e2e,
@@ -360,7 +361,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32", "fp64", "fp16", "bf16"), default="fp32")
+    ap.add_argument("--precision", choices=("fp32", "fp64", "fp16", "bf16", "fp16sr", "bf16sr"), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args(argv)

@@ -56,11 +56,15 @@ enum {
     LBM_ERR_TIMEOUT = -6   /* reserved: a bounded device wait ran out          */
 };
 
-/* Storage and arithmetic precision of the populations.  LBM_FP16 and LBM_BF16
- * store the populations in 16 bits -- f_i as its deviation f_i - w_i from the
- * rest state, g_i as it is (its rest state at T_m = 0 is zero) -- with all
- * arithmetic in FP32 and the diagnostics reductions as for LBM_FP32. */
-enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
+/* Storage and arithmetic precision of the populations.  The 16-bit modes
+ * store the populations in FP16 or BF16 -- f_i as its deviation f_i - w_i from
+ * the rest state, g_i as it is (its rest state at T_m = 0 is zero) -- with all
+ * arithmetic in FP32 and the diagnostics reductions as for LBM_FP32.
+ * LBM_FP16 / LBM_BF16 round to nearest; LBM_FP16_SR / LBM_BF16_SR round
+ * stochastically with counter-based random bits (deterministic for a given
+ * state and step), so that per-step increments below half an ulp are not
+ * lost.  Population read-back and write-back round to nearest in every mode. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3, LBM_FP16_SR = 4, LBM_BF16_SR = 5 };
 
 /* Problem kind. */
 enum {

@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libbtrirt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-Xptxas", "-warn-spills"]
-SOURCES = ["sweep_fp32.cu", "sweep_fp64.cu", "sweep_f16.cu", "lbm_api.cu"]
+SOURCES = ["sweep_fp32.cu", "sweep_fp64.cu", "sweep_f16.cu", "sweep_bf16.cu", "lbm_api.cu"]
 
 
 def _nvcc() -> str:

@@ -157,6 +157,7 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.ntx = h->ntx;
     a.rows = h->rows;
     a.prefetch = h->prefetch;
+    a.parity = h->cur;
     a.k0 = (real)h->d.k0;
     a.k1 = (real)h->d.k1;
     a.k2 = (real)h->d.k2;
@@ -386,8 +387,10 @@ template <typename Fn>
 int by_precision(int precision, Fn &&fn) {
     switch (precision) {
         case LBM_FP64: return fn(Types<double, double>{});
-        case LBM_FP16: return fn(Types<float, __half>{});
-        case LBM_BF16: return fn(Types<float, __nv_bfloat16>{});
+        case LBM_FP16: return fn(Types<float, F16<false>>{});
+        case LBM_BF16: return fn(Types<float, BF16<false>>{});
+        case LBM_FP16_SR: return fn(Types<float, F16<true>>{});
+        case LBM_BF16_SR: return fn(Types<float, BF16<true>>{});
         default: return fn(Types<float, float>{});
     }
 }
@@ -404,8 +407,9 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     if (ny > 65535) return set_err(nullptr, LBM_ERR_ARG, "ny must be <= 65535");
     if ((long long)nx * ny > (1ll << 31))
         return set_err(nullptr, LBM_ERR_ARG, "lattice larger than 2^31 cells");
-    if (precision != LBM_FP32 && precision != LBM_FP64 && precision != LBM_FP16 && precision != LBM_BF16)
-        return set_err(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64, LBM_FP32, LBM_FP16 or LBM_BF16");
+    if (precision < LBM_FP64 || precision > LBM_BF16_SR)
+        return set_err(nullptr, LBM_ERR_ARG,
+                       "precision must be LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16, LBM_FP16_SR or LBM_BF16_SR");
     lbm_s *h = new (std::nothrow) lbm_s();
     if (!h) return set_err(nullptr, LBM_ERR_OOM, "host allocation failed");
     cudaError_t e = cudaGetDevice(&h->device);

@@ -43,6 +43,7 @@ struct DevRecord {
     double valid;     // 1 once the fields of `step` have been reduced
     double counter;   // steps taken: advanced by every sweep on the device, so
                       // that replayed CUDA graphs stamp records correctly
+    double rng[2];    // stochastic-rounding step seeds, one word per buffer parity
 };
 
 // Arguments of every lattice kernel, passed by value.
@@ -56,6 +57,7 @@ struct SweepArgs {
                            // set to w_i (they are never rewritten when flow is off)
     int nx, ny;            // lattice size
     int ntx;               // number of column tiles
+    int parity;            // index of the source buffer (selects the rounding seed word)
     int rows;              // rows per block (each thread walks them)
     int prefetch;          // > 0: each block asks L2 for the tile row `prefetch`
                            // rows below its own (one bulk prefetch per block)
@@ -80,9 +82,14 @@ struct SweepArgs {
     double *oH, *oT, *oFL, *oUX, *oUY, *oRHO;
 };
 
-// Launchers, instantiated in sweep_fp32.cu / sweep_fp64.cu / sweep_f16.cu for
-// (compute real, storage S) = (float, float), (double, double),
-// (float, __half), (float, __nv_bfloat16).
+// Launchers, instantiated in sweep_fp32.cu / sweep_fp64.cu / sweep_f16.cu /
+// sweep_bf16.cu for (compute real, storage codec S) = (float, float),
+// (double, double), (float, F16<SR>), (float, BF16<SR>), SR = round to
+// nearest (false) or stochastically (true).
+template <bool SR>
+struct F16;
+template <bool SR>
+struct BF16;
 template <typename real, typename S>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
                            dim3 grid, dim3 block, cudaStream_t s);

@@ -58,38 +58,90 @@ __device__ __forceinline__ real w_of(int i) {
 // ---- storage encodings ----
 // FP32 / FP64: populations as they are.  FP16 / BF16 (arithmetic in FP32):
 // f_i is stored as its deviation f_i - w_i from the rest state (rho = 1, u = 0),
-// g_i as it is -- its rest state (solid at T_m = 0) is zero.  Rounding to the
-// 16-bit format is round-to-nearest-even.
+// g_i as it is -- its rest state (solid at T_m = 0) is zero.  The 16-bit codecs
+// round to nearest (ties to even) or, with SR, stochastically: up with
+// probability equal to the discarded fraction of an ulp, so that increments
+// smaller than half an ulp survive on average instead of stagnating.
+template <bool SR>
+struct F16 {};
+template <bool SR>
+struct BF16 {};
+
 template <typename S>
-struct Store;
+struct Store;  // elem: the stored type; ld / st: decode / encode one value
 template <>
 struct Store<float> {
-    static constexpr bool kDev = false;
+    using elem = float;
+    static constexpr bool kDev = false, kSR = false;
     __device__ static float ld(const float *p) { return __ldg(p); }
-    __device__ static void st(float *p, float v) { *p = v; }
+    __device__ static void st(float *p, float v, uint32_t) { *p = v; }
 };
 template <>
 struct Store<double> {
-    static constexpr bool kDev = false;
+    using elem = double;
+    static constexpr bool kDev = false, kSR = false;
     __device__ static double ld(const double *p) { return __ldg(p); }
-    __device__ static void st(double *p, double v) { *p = v; }
+    __device__ static void st(double *p, double v, uint32_t) { *p = v; }
 };
-template <>
-struct Store<__half> {
-    static constexpr bool kDev = true;
+template <bool SR>
+struct Store<F16<SR>> {
+    using elem = __half;
+    static constexpr bool kDev = true, kSR = SR;
     __device__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
-    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static void st(__half *p, float v, uint32_t r) {
+        if (!SR) {
+            *p = __float2half_rn(v);
+            return;
+        }
+        // toward zero, then one step away from zero with probability
+        // (|v| - |h|) / ulp, the ulp being the gap to the next magnitude
+        const __half h = __float2half_rz(v);
+        const __half h2 = __ushort_as_half((unsigned short)(__half_as_ushort(h) + 1u));
+        const float hf = __half2float(h);
+        const float ulp = fabsf(__half2float(h2) - hf);
+        const float u = (float)(r >> 8) * 0x1.0p-24f;
+        *p = (u * ulp < fabsf(v - hf)) ? h2 : h;
+    }
 };
-template <>
-struct Store<__nv_bfloat16> {
-    static constexpr bool kDev = true;
+template <bool SR>
+struct Store<BF16<SR>> {
+    using elem = __nv_bfloat16;
+    static constexpr bool kDev = true, kSR = SR;
     __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-    __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static void st(__nv_bfloat16 *p, float v, uint32_t r) {
+        if (!SR) {
+            *p = __float2bfloat16_rn(v);
+            return;
+        }
+        // bfloat16 is the upper half of a float: adding 16 random bits below
+        // the cut and truncating rounds up with the discarded fraction's odds
+        const uint32_t b = __float_as_uint(v);
+        const uint32_t t = ((b & 0x7f800000u) == 0x7f800000u) ? b : b + (r & 0xffffu);
+        *p = __ushort_as_bfloat16((unsigned short)(t >> 16));
+    }
 };
 // Offset added to a stored f value (plane i) to recover f_i.
 template <typename real, typename S>
 __device__ __forceinline__ real f_ofs(int i) {
     return Store<S>::kDev ? w_of<real>(i) : real(0);
+}
+
+// Counter-based random bits for stochastic rounding: a 32-bit integer hash
+// (Wellons' "lowbias32" finaliser) seeds each cell, xorshift32 (Marsaglia
+// 2003) steps it once per stored value.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
 }
 
 // ---- H -> (T, f_l): H_s = C_p T_m = 0, H_l = H_s + L.
@@ -221,8 +273,10 @@ __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, rea
 // b except at the tile's first / last column, where they are shifted so that
 // bL[-1] / bR[+1] land in the neighbouring tile.
 template <typename real, typename S, bool FLOW>
-__device__ __forceinline__ void pull_fast(const S *__restrict__ b, const S *__restrict__ bL,
-                                          const S *__restrict__ bR, real f[9], real g[9]) {
+__device__ __forceinline__ void pull_fast(const typename Store<S>::elem *__restrict__ b,
+                                          const typename Store<S>::elem *__restrict__ bL,
+                                          const typename Store<S>::elem *__restrict__ bR, real f[9],
+                                          real g[9]) {
     constexpr int R = kRS, W = kTW;
     using St = Store<S>;
 #define BTRIRT_PULL(P, arr, OFS)                                         \
@@ -250,7 +304,7 @@ __device__ __forceinline__ void pull_fast(const S *__restrict__ b, const S *__re
 template <typename real, typename S, int PROB, bool FLOW>
 __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y, real f[9],
                                          real g[9], real &q) {
-    const S *src = static_cast<const S *>(a.src);
+    const auto *src = static_cast<const typename Store<S>::elem *>(a.src);
     const long long self = pop_index(x, y, 0, a.ny);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -423,12 +477,12 @@ __global__ void __launch_bounds__(kReduceThreads)
 
 // Bulk prefetch of one contiguous tile row (all 18 planes, kRS values) into
 // L2: a single TMA-unit request, no registers or shared memory involved.  The
-// address is 16 B aligned (tile rows are kRS * sizeof(S) bytes apart from a
+// address is 16 B aligned (tile rows are kRS * sizeof(E) bytes apart from a
 // 256 B aligned base) and the size a multiple of 16.
-template <typename S>
-__device__ __forceinline__ void prefetch_tile_row_l2(const S *p) {
+template <typename E>
+__device__ __forceinline__ void prefetch_tile_row_l2(const E *p) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p),
-                 "r"((unsigned)(kRS * sizeof(S)))
+                 "r"((unsigned)(kRS * sizeof(E)))
                  : "memory");
 }
 
@@ -439,7 +493,8 @@ template <typename real, typename S, int PROB, bool FLOW, int MODE>
 // registers.
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     lattice_kernel(const SweepArgs<real> a) {
-    const S *src = static_cast<const S *>(a.src);
+    using E = typename Store<S>::elem;
+    const E *src = static_cast<const E *>(a.src);
     __shared__ double sh[32 * 4];
     const int lx = threadIdx.x;
     const int x = blockIdx.x * kTW + lx;
@@ -453,6 +508,16 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     // the device-side step counter (read by the diagnostics fold after this launch)
     if (MODE != kFields && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0)
         a.rec->counter += 1.0;
+    // Stochastic rounding seed of this step: read from the word of the source
+    // buffer's parity; block (0, 0) hands the next value to the other word,
+    // which only the next step reads -- no race, and graph replays see a new
+    // seed every step.
+    uint32_t step_seed = 0;
+    if (Store<S>::kSR && MODE != kFields) {
+        const double sd = a.rec->rng[a.parity];
+        if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) a.rec->rng[a.parity ^ 1] = sd + 1.0;
+        step_seed = hash32((uint32_t)(unsigned long long)sd ^ 0x5bd1e995u);
+    }
     const bool active = x < a.nx;
     // the warp's 32 columns are clear of both side walls (warp-uniform)
     const int xw = blockIdx.x * kTW + (lx & ~31);
@@ -488,11 +553,16 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
             continue;
         }
         const Macro<real> m = cell_update<real, FLOW, true>(a, f, g);
-        S *d = static_cast<S *>(a.dst) + pop_index(x, y, 0, a.ny);
+        E *d = static_cast<E *>(a.dst) + pop_index(x, y, 0, a.ny);
+        uint32_t rnd = Store<S>::kSR ? hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x)) : 0u;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            Store<S>::st(d + (9 + i) * kTW, g[i]);
-            if (FLOW) Store<S>::st(d + i * kTW, f[i] - f_ofs<real, S>(i));
+            if (Store<S>::kSR) rnd = xorshift32(rnd);
+            Store<S>::st(d + (9 + i) * kTW, g[i], rnd);
+            if (FLOW) {
+                if (Store<S>::kSR) rnd = xorshift32(rnd);
+                Store<S>::st(d + i * kTW, f[i] - f_ofs<real, S>(i), rnd);
+            }
         }
         if (MODE == kSweepDiag) {
             sfl += m.fl;
@@ -551,8 +621,9 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t v) {
 template <typename real, typename S>
 __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, double amp,
                                                    uint64_t seed) {
-    S *dst = static_cast<S *>(a.dst);
-    S *aux = static_cast<S *>(a.aux);
+    using E = typename Store<S>::elem;
+    E *dst = static_cast<E *>(a.dst);
+    E *aux = static_cast<E *>(a.aux);
     __shared__ double sh[32 * 4];
     const int x = blockIdx.x * kTW + threadIdx.x;
     const int y0 = blockIdx.y * a.rows;
@@ -567,14 +638,15 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             real T, fl;
             invert(H, a.Lh, T, fl);
             const long long c = pop_index(x, y, 0, a.ny);
-            Store<S>::st(dst + c + 9 * kTW, H - T + w_of<real>(0) * T);
+            // initial state: round to nearest (u = 0 below would round toward zero)
+            Store<S>::st(dst + c + 9 * kTW, H - T + w_of<real>(0) * T, 0x80000000u);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) Store<S>::st(dst + c + (9 + i) * kTW, w_of<real>(i) * T);
+            for (int i = 1; i < 9; ++i) Store<S>::st(dst + c + (9 + i) * kTW, w_of<real>(i) * T, 0x80000000u);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const real fi = w_of<real>(i) - f_ofs<real, S>(i);
-                Store<S>::st(dst + c + i * kTW, fi);
-                if (aux) Store<S>::st(aux + c + i * kTW, fi);
+                Store<S>::st(dst + c + i * kTW, fi, 0x80000000u);
+                if (aux) Store<S>::st(aux + c + i * kTW, fi, 0x80000000u);
             }
             sfl += fl;
             sH += H;
@@ -587,7 +659,7 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
 // Fields of the step-0 state (no streaming; u = 0 by definition).
 template <typename real, typename S, bool FLOW>
 __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
-    const S *src = static_cast<const S *>(a.src);
+    const auto *src = static_cast<const typename Store<S>::elem *>(a.src);
     const int x = blockIdx.x * kTW + threadIdx.x;
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
@@ -620,8 +692,9 @@ __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
 template <typename S>
 __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, int ny,
                               bool to_staging) {
-    using real = typename std::conditional<sizeof(S) == 8, double, float>::type;
-    S *buf = static_cast<S *>(bufv), *buf2 = static_cast<S *>(buf2v);
+    using E = typename Store<S>::elem;
+    using real = typename std::conditional<sizeof(E) == 8, double, float>::type;
+    E *buf = static_cast<E *>(bufv), *buf2 = static_cast<E *>(buf2v);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= nx) return;
@@ -634,8 +707,9 @@ __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, in
             stage[p * P + o] = (double)(Store<S>::ld(buf + c + p * kTW) + ofs);
         } else {
             const real v = (real)stage[p * P + o] - ofs;
-            Store<S>::st(buf + c + p * kTW, v);
-            if (buf2 && p < 9) Store<S>::st(buf2 + c + p * kTW, v);
+            // caller data: stochastic codecs round it to nearest as well
+            Store<S>::st(buf + c + p * kTW, v, 0x80000000u);
+            if (buf2 && p < 9) Store<S>::st(buf2 + c + p * kTW, v, 0x80000000u);
         }
     }
 }

@@ -1,7 +1,7 @@
-// 16-bit population storage (FP16 and BF16) with FP32 arithmetic.
+// FP16 population storage with FP32 arithmetic (round to nearest / stochastic).
 #include "sweep.cuh"
 
 namespace btrirt {
-BTRIRT_INSTANTIATE(float, __half)
-BTRIRT_INSTANTIATE(float, __nv_bfloat16)
+BTRIRT_INSTANTIATE(float, F16<false>)
+BTRIRT_INSTANTIATE(float, F16<true>)
 }  // namespace btrirt

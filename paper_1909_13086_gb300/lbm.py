@@ -21,11 +21,12 @@ LIB_PATH = os.path.join(_PKG, "libbtrirt.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE, LBM_ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6
-LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16 = 0, 1, 2, 3
+LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16, LBM_FP16_SR, LBM_BF16_SR = 0, 1, 2, 3, 4, 5
 LBM_CAVITY, LBM_STEFAN = 0, 1
 FIELD_BITS = {"H": 1, "T": 2, "fl": 4, "ux": 8, "uy": 16, "rho": 32}
 FIELD_NAMES = ("H", "T", "fl", "ux", "uy", "rho")
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16,
+              "fp16sr": LBM_FP16_SR, "bf16sr": LBM_BF16_SR}
 
 
 class LbmError(RuntimeError):
