@@ -83,6 +83,11 @@ struct Store<double> {
     __device__ static double ld(const double *p) { return __ldg(p); }
     __device__ static void st(double *p, double v, uint32_t) { *p = v; }
 };
+// Stochastic rounding by "add random bits below the cut, then truncate": a
+// float's bit pattern plus a uniform integer below the first discarded bit,
+// truncated toward zero, rounds the magnitude up with probability equal to the
+// discarded fraction (a carry into the exponent is the correct round-up).  r is
+// 16 random bits.
 template <bool SR>
 struct Store<F16<SR>> {
     using elem = __half;
@@ -93,14 +98,21 @@ struct Store<F16<SR>> {
             *p = __float2half_rn(v);
             return;
         }
-        // toward zero, then one step away from zero with probability
-        // (|v| - |h|) / ulp, the ulp being the gap to the next magnitude
-        const __half h = __float2half_rz(v);
-        const __half h2 = __ushort_as_half((unsigned short)(__half_as_ushort(h) + 1u));
-        const float hf = __half2float(h);
-        const float ulp = fabsf(__half2float(h2) - hf);
-        const float u = (float)(r >> 8) * 0x1.0p-24f;
-        *p = (u * ulp < fabsf(v - hf)) ? h2 : h;
+        const uint32_t b = __float_as_uint(v);
+        const int e = (int)((b >> 23) & 0xffu);  // biased float exponent
+        uint32_t t;
+        if (e >= 113 && e != 255) {
+            t = b + (r >> 3);  // FP16 normal range: 13 bits discarded
+        } else if (e >= 103 && e < 113) {
+            // FP16 subnormal range: 126 - e bits (14..23) discarded; the lowest
+            // ones get no random bits (a bias below 2^-16 ulp)
+            const int sh = 126 - e;
+            t = b + (sh >= 16 ? (r << (sh - 16)) : (r >> (16 - sh)));
+        } else {
+            *p = __float2half_rn(v);  // |v| < 2^-24, Inf or NaN
+            return;
+        }
+        *p = __float2half_rz(__uint_as_float(t));
     }
 };
 template <bool SR>
@@ -113,13 +125,16 @@ struct Store<BF16<SR>> {
             *p = __float2bfloat16_rn(v);
             return;
         }
-        // bfloat16 is the upper half of a float: adding 16 random bits below
-        // the cut and truncating rounds up with the discarded fraction's odds
+        // bfloat16 is the upper half of a float: 16 bits discarded
         const uint32_t b = __float_as_uint(v);
-        const uint32_t t = ((b & 0x7f800000u) == 0x7f800000u) ? b : b + (r & 0xffffu);
+        const uint32_t t = ((b & 0x7f800000u) == 0x7f800000u) ? b : b + r;
         *p = __ushort_as_bfloat16((unsigned short)(t >> 16));
     }
 };
+// Random input that makes the stochastic codecs round to nearest (half of the
+// 16-bit range): used for the initial state and caller data.
+constexpr uint32_t kHalfR = 0x8000u;
+
 // Offset added to a stored f value (plane i) to recover f_i.
 template <typename real, typename S>
 __device__ __forceinline__ real f_ofs(int i) {
@@ -554,15 +569,14 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
         }
         const Macro<real> m = cell_update<real, FLOW, true>(a, f, g);
         E *d = static_cast<E *>(a.dst) + pop_index(x, y, 0, a.ny);
+        // one xorshift step gives the 16 random bits of g_i (low half) and f_i
+        // (high half)
         uint32_t rnd = Store<S>::kSR ? hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x)) : 0u;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (Store<S>::kSR) rnd = xorshift32(rnd);
-            Store<S>::st(d + (9 + i) * kTW, g[i], rnd);
-            if (FLOW) {
-                if (Store<S>::kSR) rnd = xorshift32(rnd);
-                Store<S>::st(d + i * kTW, f[i] - f_ofs<real, S>(i), rnd);
-            }
+            Store<S>::st(d + (9 + i) * kTW, g[i], rnd & 0xffffu);
+            if (FLOW) Store<S>::st(d + i * kTW, f[i] - f_ofs<real, S>(i), rnd >> 16);
         }
         if (MODE == kSweepDiag) {
             sfl += m.fl;
@@ -638,15 +652,15 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             real T, fl;
             invert(H, a.Lh, T, fl);
             const long long c = pop_index(x, y, 0, a.ny);
-            // initial state: round to nearest (u = 0 below would round toward zero)
-            Store<S>::st(dst + c + 9 * kTW, H - T + w_of<real>(0) * T, 0x80000000u);
+            // initial state: round to nearest
+            Store<S>::st(dst + c + 9 * kTW, H - T + w_of<real>(0) * T, kHalfR);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) Store<S>::st(dst + c + (9 + i) * kTW, w_of<real>(i) * T, 0x80000000u);
+            for (int i = 1; i < 9; ++i) Store<S>::st(dst + c + (9 + i) * kTW, w_of<real>(i) * T, kHalfR);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const real fi = w_of<real>(i) - f_ofs<real, S>(i);
-                Store<S>::st(dst + c + i * kTW, fi, 0x80000000u);
-                if (aux) Store<S>::st(aux + c + i * kTW, fi, 0x80000000u);
+                Store<S>::st(dst + c + i * kTW, fi, kHalfR);
+                if (aux) Store<S>::st(aux + c + i * kTW, fi, kHalfR);
             }
             sfl += fl;
             sH += H;
@@ -708,8 +722,8 @@ __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, in
         } else {
             const real v = (real)stage[p * P + o] - ofs;
             // caller data: stochastic codecs round it to nearest as well
-            Store<S>::st(buf + c + p * kTW, v, 0x80000000u);
-            if (buf2 && p < 9) Store<S>::st(buf2 + c + p * kTW, v, 0x80000000u);
+            Store<S>::st(buf + c + p * kTW, v, kHalfR);
+            if (buf2 && p < 9) Store<S>::st(buf2 + c + p * kTW, v, kHalfR);
         }
     }
 }
