@@ -59,7 +59,9 @@ enum {
 /* Storage and arithmetic precision of the populations.  The 16-bit modes
  * store the populations in FP16 or BF16 -- f_i as its deviation f_i - w_i from
  * the rest state, g_i as it is (its rest state at T_m = 0 is zero) -- with all
- * arithmetic in FP32 and the diagnostics reductions as for LBM_FP32.
+ * arithmetic in FP32 and the diagnostics reductions as for LBM_FP32.  FP16
+ * values are stored scaled by exact powers of two (g by 2^6, f - w by 2^10) so
+ * that they stay in FP16's normal range: |g| <= 1000 and |f - w| <= 64.
  * LBM_FP16 / LBM_BF16 round to nearest; LBM_FP16_SR / LBM_BF16_SR round
  * stochastically with counter-based random bits (deterministic for a given
  * state and step), so that per-step increments below half an ulp are not

@@ -67,72 +67,73 @@ struct F16 {};
 template <bool SR>
 struct BF16 {};
 
+// Each codec decodes / encodes an f plane (ldf / stf: the stored value is
+// f_i - w_i for the 16-bit codecs, see f_ofs) or a g plane (ldg / stg).
 template <typename S>
-struct Store;  // elem: the stored type; ld / st: decode / encode one value
+struct Store;
 template <>
 struct Store<float> {
     using elem = float;
     static constexpr bool kDev = false, kSR = false;
-    __device__ static float ld(const float *p) { return __ldg(p); }
-    __device__ static void st(float *p, float v, uint32_t) { *p = v; }
+    __device__ static float ldf(const float *p) { return __ldg(p); }
+    __device__ static float ldg(const float *p) { return __ldg(p); }
+    __device__ static void stf(float *p, float v, uint32_t) { *p = v; }
+    __device__ static void stg(float *p, float v, uint32_t) { *p = v; }
 };
 template <>
 struct Store<double> {
     using elem = double;
     static constexpr bool kDev = false, kSR = false;
-    __device__ static double ld(const double *p) { return __ldg(p); }
-    __device__ static void st(double *p, double v, uint32_t) { *p = v; }
+    __device__ static double ldf(const double *p) { return __ldg(p); }
+    __device__ static double ldg(const double *p) { return __ldg(p); }
+    __device__ static void stf(double *p, double v, uint32_t) { *p = v; }
+    __device__ static void stg(double *p, double v, uint32_t) { *p = v; }
 };
+
 // Stochastic rounding by "add random bits below the cut, then truncate": a
 // float's bit pattern plus a uniform integer below the first discarded bit,
 // truncated toward zero, rounds the magnitude up with probability equal to the
 // discarded fraction (a carry into the exponent is the correct round-up).  r is
-// 16 random bits.
+// 16 random bits; NaN and Inf pass through unchanged.
+__device__ __forceinline__ uint32_t sr_bits(float v, uint32_t add) {
+    const uint32_t b = __float_as_uint(v);
+    return ((b & 0x7f800000u) == 0x7f800000u) ? b : b + add;
+}
+
+// FP16 is stored scaled by a power of two (exact): g by 2^6, f - w by 2^10, so
+// that the working values sit in FP16's normal range (g down to ~1e-6, f - w
+// down to ~6e-8) while g up to 1000 (latent heat 1/Ste included) and |f - w| up
+// to 64 still fit.  In the normal range 13 float mantissa bits are discarded.
 template <bool SR>
 struct Store<F16<SR>> {
     using elem = __half;
     static constexpr bool kDev = true, kSR = SR;
-    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
-    __device__ static void st(__half *p, float v, uint32_t r) {
-        if (!SR) {
-            *p = __float2half_rn(v);
-            return;
-        }
-        const uint32_t b = __float_as_uint(v);
-        const int e = (int)((b >> 23) & 0xffu);  // biased float exponent
-        uint32_t t;
-        if (e >= 113 && e != 255) {
-            t = b + (r >> 3);  // FP16 normal range: 13 bits discarded
-        } else if (e >= 103 && e < 113) {
-            // FP16 subnormal range: 126 - e bits (14..23) discarded; the lowest
-            // ones get no random bits (a bias below 2^-16 ulp)
-            const int sh = 126 - e;
-            t = b + (sh >= 16 ? (r << (sh - 16)) : (r >> (16 - sh)));
-        } else {
-            *p = __float2half_rn(v);  // |v| < 2^-24, Inf or NaN
-            return;
-        }
-        *p = __float2half_rz(__uint_as_float(t));
+    static constexpr float kG = 64.0f, kF = 1024.0f;
+    __device__ static float dec(const __half *p, float inv) { return __half2float(__ldg(p)) * inv; }
+    __device__ static void enc(__half *p, float v, uint32_t r) {
+        *p = SR ? __float2half_rz(__uint_as_float(sr_bits(v, r >> 3))) : __float2half_rn(v);
     }
+    __device__ static float ldf(const __half *p) { return dec(p, 1.0f / kF); }
+    __device__ static float ldg(const __half *p) { return dec(p, 1.0f / kG); }
+    __device__ static void stf(__half *p, float v, uint32_t r) { enc(p, v * kF, r); }
+    __device__ static void stg(__half *p, float v, uint32_t r) { enc(p, v * kG, r); }
 };
+// BF16 has FP32's exponent range, so no scaling; 16 bits are discarded.
 template <bool SR>
 struct Store<BF16<SR>> {
     using elem = __nv_bfloat16;
     static constexpr bool kDev = true, kSR = SR;
     __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static void st(__nv_bfloat16 *p, float v, uint32_t r) {
-        if (!SR) {
-            *p = __float2bfloat16_rn(v);
-            return;
-        }
-        // bfloat16 is the upper half of a float: 16 bits discarded
-        const uint32_t b = __float_as_uint(v);
-        const uint32_t t = ((b & 0x7f800000u) == 0x7f800000u) ? b : b + r;
-        *p = __ushort_as_bfloat16((unsigned short)(t >> 16));
+        *p = SR ? __ushort_as_bfloat16((unsigned short)(sr_bits(v, r) >> 16)) : __float2bfloat16_rn(v);
     }
+    __device__ static float ldf(const __nv_bfloat16 *p) { return ld(p); }
+    __device__ static float ldg(const __nv_bfloat16 *p) { return ld(p); }
+    __device__ static void stf(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
+    __device__ static void stg(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
 };
 // Random input that makes the stochastic codecs round to nearest (half of the
-// 16-bit range): used for the initial state and caller data.
+// 16-bit range; ties away from zero): used for the initial state and caller data.
 constexpr uint32_t kHalfR = 0x8000u;
 
 // Offset added to a stored f value (plane i) to recover f_i.
@@ -294,21 +295,21 @@ __device__ __forceinline__ void pull_fast(const typename Store<S>::elem *__restr
                                           real g[9]) {
     constexpr int R = kRS, W = kTW;
     using St = Store<S>;
-#define BTRIRT_PULL(P, arr, OFS)                                         \
-    arr[0] = St::ld(b + (P + 0) * W) + OFS(0);                           \
-    arr[1] = St::ld(bL + (P + 1) * W - 1) + OFS(1);                      \
-    arr[2] = St::ld(b + (P + 2) * W - R) + OFS(2);                       \
-    arr[3] = St::ld(bR + (P + 3) * W + 1) + OFS(3);                      \
-    arr[4] = St::ld(b + (P + 4) * W + R) + OFS(4);                       \
-    arr[5] = St::ld(bL + (P + 5) * W - R - 1) + OFS(5);                  \
-    arr[6] = St::ld(bR + (P + 6) * W - R + 1) + OFS(6);                  \
-    arr[7] = St::ld(bR + (P + 7) * W + R + 1) + OFS(7);                  \
-    arr[8] = St::ld(bL + (P + 8) * W + R - 1) + OFS(8);
+#define BTRIRT_PULL(P, arr, LD, OFS)                                     \
+    arr[0] = St::LD(b + (P + 0) * W) + OFS(0);                           \
+    arr[1] = St::LD(bL + (P + 1) * W - 1) + OFS(1);                      \
+    arr[2] = St::LD(b + (P + 2) * W - R) + OFS(2);                       \
+    arr[3] = St::LD(bR + (P + 3) * W + 1) + OFS(3);                      \
+    arr[4] = St::LD(b + (P + 4) * W + R) + OFS(4);                       \
+    arr[5] = St::LD(bL + (P + 5) * W - R - 1) + OFS(5);                  \
+    arr[6] = St::LD(bR + (P + 6) * W - R + 1) + OFS(6);                  \
+    arr[7] = St::LD(bR + (P + 7) * W + R + 1) + OFS(7);                  \
+    arr[8] = St::LD(bL + (P + 8) * W + R - 1) + OFS(8);
 #define BTRIRT_NOOFS(i) real(0)
 #define BTRIRT_FOFS(i) f_ofs<real, S>(i)
-    BTRIRT_PULL(9, g, BTRIRT_NOOFS)
+    BTRIRT_PULL(9, g, ldg, BTRIRT_NOOFS)
     if (FLOW) {
-        BTRIRT_PULL(0, f, BTRIRT_FOFS)
+        BTRIRT_PULL(0, f, ldf, BTRIRT_FOFS)
     }
 #undef BTRIRT_PULL
 #undef BTRIRT_NOOFS
@@ -329,8 +330,8 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
         const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
         const long long cell = in ? pop_index(sx, sy, 0, a.ny) : self;
         const int pl = in ? i : opp_of(i);
-        real gv = Store<S>::ld(src + cell + (9 + pl) * kTW);
-        if (FLOW) f[i] = Store<S>::ld(src + cell + pl * kTW) + f_ofs<real, S>(pl);
+        real gv = Store<S>::ldg(src + cell + (9 + pl) * kTW);
+        if (FLOW) f[i] = Store<S>::ldf(src + cell + pl * kTW) + f_ofs<real, S>(pl);
         if (!in) {
             bool heated;
             if (PROB == kStefan) {
@@ -575,8 +576,8 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (Store<S>::kSR) rnd = xorshift32(rnd);
-            Store<S>::st(d + (9 + i) * kTW, g[i], rnd & 0xffffu);
-            if (FLOW) Store<S>::st(d + i * kTW, f[i] - f_ofs<real, S>(i), rnd >> 16);
+            Store<S>::stg(d + (9 + i) * kTW, g[i], rnd & 0xffffu);
+            if (FLOW) Store<S>::stf(d + i * kTW, f[i] - f_ofs<real, S>(i), rnd >> 16);
         }
         if (MODE == kSweepDiag) {
             sfl += m.fl;
@@ -653,14 +654,14 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             invert(H, a.Lh, T, fl);
             const long long c = pop_index(x, y, 0, a.ny);
             // initial state: round to nearest
-            Store<S>::st(dst + c + 9 * kTW, H - T + w_of<real>(0) * T, kHalfR);
+            Store<S>::stg(dst + c + 9 * kTW, H - T + w_of<real>(0) * T, kHalfR);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) Store<S>::st(dst + c + (9 + i) * kTW, w_of<real>(i) * T, kHalfR);
+            for (int i = 1; i < 9; ++i) Store<S>::stg(dst + c + (9 + i) * kTW, w_of<real>(i) * T, kHalfR);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const real fi = w_of<real>(i) - f_ofs<real, S>(i);
-                Store<S>::st(dst + c + i * kTW, fi, kHalfR);
-                if (aux) Store<S>::st(aux + c + i * kTW, fi, kHalfR);
+                Store<S>::stf(dst + c + i * kTW, fi, kHalfR);
+                if (aux) Store<S>::stf(aux + c + i * kTW, fi, kHalfR);
             }
             sfl += fl;
             sH += H;
@@ -682,12 +683,12 @@ __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
         const long long c = pop_index(x, y, 0, a.ny);
         real g[9], H, rho = real(1);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = Store<S>::ld(src + c + (9 + i) * kTW);
+        for (int i = 0; i < 9; ++i) g[i] = Store<S>::ldg(src + c + (9 + i) * kTW);
         H = sum9(g);
         if (FLOW) {
             real f[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = Store<S>::ld(src + c + i * kTW) + f_ofs<real, S>(i);
+            for (int i = 0; i < 9; ++i) f[i] = Store<S>::ldf(src + c + i * kTW) + f_ofs<real, S>(i);
             rho = sum9(f);
         }
         real T, fl;
@@ -716,14 +717,20 @@ __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, in
     const long long P = (long long)nx * ny, o = (long long)y * nx + x;
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
-        const real ofs = p < 9 ? f_ofs<real, S>(p) : real(0);
+        const bool isf = p < 9;
+        const real ofs = isf ? f_ofs<real, S>(p) : real(0);
+        E *q = buf + c + p * kTW;
         if (to_staging) {
-            stage[p * P + o] = (double)(Store<S>::ld(buf + c + p * kTW) + ofs);
+            stage[p * P + o] = (double)((isf ? Store<S>::ldf(q) : Store<S>::ldg(q)) + ofs);
         } else {
             const real v = (real)stage[p * P + o] - ofs;
             // caller data: stochastic codecs round it to nearest as well
-            Store<S>::st(buf + c + p * kTW, v, kHalfR);
-            if (buf2 && p < 9) Store<S>::st(buf2 + c + p * kTW, v, kHalfR);
+            if (isf) {
+                Store<S>::stf(q, v, kHalfR);
+                if (buf2) Store<S>::stf(buf2 + c + p * kTW, v, kHalfR);
+            } else {
+                Store<S>::stg(q, v, kHalfR);
+            }
         }
     }
 }
