@@ -79,6 +79,8 @@ struct Store<float> {
     __device__ static float ldg(const float *p) { return __ldg(p); }
     __device__ static void stf(float *p, float v, uint32_t) { *p = v; }
     __device__ static void stg(float *p, float v, uint32_t) { *p = v; }
+    __device__ static void stf_rn(float *p, float v) { *p = v; }
+    __device__ static void stg_rn(float *p, float v) { *p = v; }
 };
 template <>
 struct Store<double> {
@@ -88,16 +90,19 @@ struct Store<double> {
     __device__ static double ldg(const double *p) { return __ldg(p); }
     __device__ static void stf(double *p, double v, uint32_t) { *p = v; }
     __device__ static void stg(double *p, double v, uint32_t) { *p = v; }
+    __device__ static void stf_rn(double *p, double v) { *p = v; }
+    __device__ static void stg_rn(double *p, double v) { *p = v; }
 };
 
 // Stochastic rounding by "add random bits below the cut, then truncate": a
 // float's bit pattern plus a uniform integer below the first discarded bit,
 // truncated toward zero, rounds the magnitude up with probability equal to the
 // discarded fraction (a carry into the exponent is the correct round-up).  r is
-// 16 random bits; NaN and Inf pass through unchanged.
-__device__ __forceinline__ uint32_t sr_bits(float v, uint32_t add) {
-    const uint32_t b = __float_as_uint(v);
-    return ((b & 0x7f800000u) == 0x7f800000u) ? b : b + add;
+// 16 random bits.  Only finite values may take this path (the sweep checks
+// each cell and stores a non-finite cell with the _rn encoders, so that NaN
+// stays NaN).
+__device__ __forceinline__ float sr_add(float v, uint32_t add) {
+    return __uint_as_float(__float_as_uint(v) + add);
 }
 
 // FP16 is stored scaled by a power of two (exact): g by 2^6, f - w by 2^10, so
@@ -109,14 +114,15 @@ struct Store<F16<SR>> {
     using elem = __half;
     static constexpr bool kDev = true, kSR = SR;
     static constexpr float kG = 64.0f, kF = 1024.0f;
-    __device__ static float dec(const __half *p, float inv) { return __half2float(__ldg(p)) * inv; }
     __device__ static void enc(__half *p, float v, uint32_t r) {
-        *p = SR ? __float2half_rz(__uint_as_float(sr_bits(v, r >> 3))) : __float2half_rn(v);
+        *p = SR ? __float2half_rz(sr_add(v, r >> 3)) : __float2half_rn(v);
     }
-    __device__ static float ldf(const __half *p) { return dec(p, 1.0f / kF); }
-    __device__ static float ldg(const __half *p) { return dec(p, 1.0f / kG); }
+    __device__ static float ldf(const __half *p) { return __half2float(__ldg(p)) * (1.0f / kF); }
+    __device__ static float ldg(const __half *p) { return __half2float(__ldg(p)) * (1.0f / kG); }
     __device__ static void stf(__half *p, float v, uint32_t r) { enc(p, v * kF, r); }
     __device__ static void stg(__half *p, float v, uint32_t r) { enc(p, v * kG, r); }
+    __device__ static void stf_rn(__half *p, float v) { *p = __float2half_rn(v * kF); }
+    __device__ static void stg_rn(__half *p, float v) { *p = __float2half_rn(v * kG); }
 };
 // BF16 has FP32's exponent range, so no scaling; 16 bits are discarded.
 template <bool SR>
@@ -125,17 +131,16 @@ struct Store<BF16<SR>> {
     static constexpr bool kDev = true, kSR = SR;
     __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static void st(__nv_bfloat16 *p, float v, uint32_t r) {
-        *p = SR ? __ushort_as_bfloat16((unsigned short)(sr_bits(v, r) >> 16)) : __float2bfloat16_rn(v);
+        *p = SR ? __ushort_as_bfloat16((unsigned short)(__float_as_uint(sr_add(v, r)) >> 16))
+                : __float2bfloat16_rn(v);
     }
     __device__ static float ldf(const __nv_bfloat16 *p) { return ld(p); }
     __device__ static float ldg(const __nv_bfloat16 *p) { return ld(p); }
     __device__ static void stf(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
     __device__ static void stg(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
+    __device__ static void stf_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static void stg_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
-// Random input that makes the stochastic codecs round to nearest (half of the
-// 16-bit range; ties away from zero): used for the initial state and caller data.
-constexpr uint32_t kHalfR = 0x8000u;
-
 // Offset added to a stored f value (plane i) to recover f_i.
 template <typename real, typename S>
 __device__ __forceinline__ real f_ofs(int i) {
@@ -143,8 +148,9 @@ __device__ __forceinline__ real f_ofs(int i) {
 }
 
 // Counter-based random bits for stochastic rounding: a 32-bit integer hash
-// (Wellons' "lowbias32" finaliser) seeds each cell, xorshift32 (Marsaglia
-// 2003) steps it once per stored value.
+// (Wellons' "lowbias32" finaliser) of the step seed and the cell index seeds a
+// linear congruential generator (Numerical Recipes' constants), stepped once
+// per stored value; its top 16 bits are used.
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352du;
@@ -153,11 +159,9 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16;
     return x;
 }
-__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
-    x ^= x << 13;
-    x ^= x >> 17;
-    x ^= x << 5;
-    return x;
+__device__ __forceinline__ uint32_t lcg_next(uint32_t &s) {
+    s = s * 1664525u + 1013904223u;
+    return s >> 16;
 }
 
 // ---- H -> (T, f_l): H_s = C_p T_m = 0, H_l = H_s + L.
@@ -570,14 +574,19 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
         }
         const Macro<real> m = cell_update<real, FLOW, true>(a, f, g);
         E *d = static_cast<E *>(a.dst) + pop_index(x, y, 0, a.ny);
-        // one xorshift step gives the 16 random bits of g_i (low half) and f_i
-        // (high half)
-        uint32_t rnd = Store<S>::kSR ? hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x)) : 0u;
+        if (!Store<S>::kSR || !(isfinite(m.H) && isfinite(m.rho))) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if (Store<S>::kSR) rnd = xorshift32(rnd);
-            Store<S>::stg(d + (9 + i) * kTW, g[i], rnd & 0xffffu);
-            if (FLOW) Store<S>::stf(d + i * kTW, f[i] - f_ofs<real, S>(i), rnd >> 16);
+            for (int i = 0; i < 9; ++i) {
+                Store<S>::stg_rn(d + (9 + i) * kTW, g[i]);
+                if (FLOW) Store<S>::stf_rn(d + i * kTW, f[i] - f_ofs<real, S>(i));
+            }
+        } else {
+            uint32_t rs = hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x));
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                Store<S>::stg(d + (9 + i) * kTW, g[i], lcg_next(rs));
+                if (FLOW) Store<S>::stf(d + i * kTW, f[i] - f_ofs<real, S>(i), lcg_next(rs));
+            }
         }
         if (MODE == kSweepDiag) {
             sfl += m.fl;
@@ -653,15 +662,15 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             real T, fl;
             invert(H, a.Lh, T, fl);
             const long long c = pop_index(x, y, 0, a.ny);
-            // initial state: round to nearest
-            Store<S>::stg(dst + c + 9 * kTW, H - T + w_of<real>(0) * T, kHalfR);
+            // initial state: rounded to nearest
+            Store<S>::stg_rn(dst + c + 9 * kTW, H - T + w_of<real>(0) * T);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) Store<S>::stg(dst + c + (9 + i) * kTW, w_of<real>(i) * T, kHalfR);
+            for (int i = 1; i < 9; ++i) Store<S>::stg_rn(dst + c + (9 + i) * kTW, w_of<real>(i) * T);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const real fi = w_of<real>(i) - f_ofs<real, S>(i);
-                Store<S>::stf(dst + c + i * kTW, fi, kHalfR);
-                if (aux) Store<S>::stf(aux + c + i * kTW, fi, kHalfR);
+                Store<S>::stf_rn(dst + c + i * kTW, fi);
+                if (aux) Store<S>::stf_rn(aux + c + i * kTW, fi);
             }
             sfl += fl;
             sH += H;
@@ -726,10 +735,10 @@ __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, in
             const real v = (real)stage[p * P + o] - ofs;
             // caller data: stochastic codecs round it to nearest as well
             if (isf) {
-                Store<S>::stf(q, v, kHalfR);
-                if (buf2) Store<S>::stf(buf2 + c + p * kTW, v, kHalfR);
+                Store<S>::stf_rn(q, v);
+                if (buf2) Store<S>::stf_rn(buf2 + c + p * kTW, v);
             } else {
-                Store<S>::stg(q, v, kHalfR);
+                Store<S>::stg_rn(q, v);
             }
         }
     }
