@@ -181,6 +181,47 @@ int lbm_read_populations(lbm_handle h, double *f, double *g, long long *step);
  * undefined until the next step. */
 int lbm_write_populations(lbm_handle h, const double *f, const double *g, long long step);
 
+/* ---- Batches: many lattices advanced together ------------------------------
+ * A batch advances all its lattices by one fused launch per step: the blocks
+ * of every member lattice form one grid (each block looks up its lattice and
+ * tile in a device table), so lattices too small to fill the GPU alone -- the
+ * 256 x 128 requests of a serving stream -- share it, and the per-step launch
+ * cost is paid once.  The batch replays CUDA graphs of 64-step chunks (captured
+ * once per batch composition).  Each step of a member computes exactly what
+ * lbm_step would: the results are bitwise those of stepping it alone.
+ *
+ * Members keep their own memory and state; lbm_diagnostics, lbm_read_fields
+ * and friends keep working on them between batch steps.  Every member must
+ * share the device, precision, problem kind and flow_on of the first one; the
+ * last step of each lbm_batch_step is a diagnostic step for every member (their
+ * diag_every setting does not apply inside a batch).  The batch orders its
+ * work after what is queued on the members' streams and their streams after
+ * it.  Errors of batch calls are reported by lbm_last_error(NULL). */
+typedef struct lbm_batch_s *lbm_batch;
+
+/* Create an empty batch for up to max_lattices lattices (1..65536) on the
+ * current device; cuda_stream as in lbm_create.  Allocates the device table
+ * (through the allocator hook if one is installed).  Errors: LBM_ERR_ARG,
+ * LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_batch_create(int max_lattices, void *cuda_stream, lbm_batch *out);
+
+/* Add a lattice (its parameters set) to the batch / remove it.  Membership
+ * changes take effect at the next lbm_batch_step (the table is rebuilt and the
+ * chunk graph re-captured then).  Errors: LBM_ERR_ARG (full, duplicate, not a
+ * member, or precision / problem / flow_on differing from the batch's),
+ * LBM_ERR_STATE (no parameters). */
+int lbm_batch_add(lbm_batch b, lbm_handle h);
+int lbm_batch_remove(lbm_batch b, lbm_handle h);
+
+/* Number of lattices in the batch. */
+int lbm_batch_count(lbm_batch b, int *count);
+
+/* Advance every member n >= 0 steps, asynchronously on the batch's stream. */
+int lbm_batch_step(lbm_batch b, long long n);
+
+/* Free the batch (not its members). */
+int lbm_batch_destroy(lbm_batch b);
+
 /* One step with no allocation, for callers that cannot allocate device
  * memory at the moment they step -- code running while a stream is being
  * captured into a CUDA graph (where cudaMalloc is not allowed), hosts that

@@ -661,6 +661,267 @@ const char *lbm_version(void) { return "btrirt 0.1 sm_103a"; }
 
 }  // extern "C"
 
+
+// ---------------------------------------------------------------------------
+// Batches: many lattices advanced by one launch per step.
+// ---------------------------------------------------------------------------
+struct lbm_batch_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int max = 0;
+    std::vector<lbm_s *> members;
+    void *entries = nullptr;  // device table: max BatchEntry<real>
+    int *parity = nullptr;    // device: source buffer of each member
+    std::vector<unsigned char> host_entries;
+    std::vector<int> host_parity;
+    int nblocks = 0;
+    bool dirty = true;        // table must be rebuilt and uploaded
+    int precision = -1, problem = -1, flow = -1;
+    int graph_chunk = 64;     // even: parities return to their start value
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev = nullptr;
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn release = nullptr;
+    void *alloc_ctx = nullptr;
+};
+
+namespace {
+
+int batch_err(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_error, sizeof(g_create_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define BATCH_TRY(call)                                                                         \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return batch_err(LBM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void batch_free(lbm_batch_s *b, void *p) {
+    if (!p) return;
+    if (b->release) b->release(p, b->alloc_ctx); else cudaFree(p);
+}
+
+void batch_drop_graph(lbm_batch_s *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+template <typename real>
+size_t entry_bytes() { return sizeof(BatchEntry<real>); }
+
+template <typename real>
+void batch_build(lbm_batch_s *b) {
+    const size_t eb = entry_bytes<real>();
+    b->host_entries.assign(eb * b->members.size(), 0);
+    int start = 0;
+    for (size_t r = 0; r < b->members.size(); ++r) {
+        lbm_s *h = b->members[r];
+        BatchEntry<real> e{};
+        for (int p = 0; p < 2; ++p) {
+            e.a[p] = make_args<real>(h, h->buf[p], h->buf[p ^ 1]);
+            e.a[p].parity = p;
+        }
+        e.start = start;
+        e.gx = (int)h->grid.x;
+        e.gy = (int)h->grid.y;
+        start += e.gx * e.gy;
+        std::memcpy(b->host_entries.data() + r * eb, &e, eb);
+    }
+    b->nblocks = start;
+}
+
+template <typename real, typename S>
+int batch_steps(lbm_batch_s *b, long long n) {
+    const int nm = (int)b->members.size();
+    if (b->dirty) {
+        batch_build<real>(b);
+        BATCH_TRY(cudaMemcpyAsync(b->entries, b->host_entries.data(), b->host_entries.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+        batch_drop_graph(b);
+        b->dirty = false;
+    }
+    b->host_parity.resize(nm);
+    for (int r = 0; r < nm; ++r) b->host_parity[r] = b->members[r]->cur;
+    BATCH_TRY(cudaMemcpyAsync(b->parity, b->host_parity.data(), nm * sizeof(int), cudaMemcpyHostToDevice,
+                              b->stream));
+    long long done = 0;
+    const int K = b->graph_chunk;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    BATCH_TRY(cudaStreamIsCapturing(b->stream, &st));
+    const bool graphs = K >= 2 && st == cudaStreamCaptureStatusNone;
+    while (graphs && n - done > K) {
+        if (!b->graph) {
+            BATCH_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int j = 0; j < K && e == cudaSuccess; ++j)
+                e = launch_batch<real, S>(b->entries, b->parity, nm, b->nblocks, b->problem, b->flow != 0,
+                                          false, j, b->stream);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return batch_err(LBM_ERR_CUDA, "batch graph capture failed: %s",
+                                 cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            const cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e3 != cudaSuccess) {
+                b->graph = nullptr;
+                return batch_err(LBM_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e3));
+            }
+        }
+        BATCH_TRY(cudaGraphLaunch(b->graph, b->stream));
+        done += K;
+    }
+    for (; done < n; ++done) {
+        const cudaError_t e = launch_batch<real, S>(b->entries, b->parity, nm, b->nblocks, b->problem,
+                                                    b->flow != 0, done == n - 1, (int)(done & 1), b->stream);
+        if (e != cudaSuccess) return batch_err(LBM_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+    }
+    for (lbm_s *h : b->members) {
+        h->step += n;
+        h->cur ^= (int)(n & 1);
+        h->has_prev = true;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int max_lattices, void *cuda_stream, lbm_batch *out) {
+    if (!out || max_lattices < 1 || max_lattices > 65536)
+        return batch_err(LBM_ERR_ARG, "lbm_batch_create: need out != NULL and 1 <= max_lattices <= 65536");
+    *out = nullptr;
+    lbm_batch_s *b = new (std::nothrow) lbm_batch_s();
+    if (!b) return batch_err(LBM_ERR_OOM, "host allocation failed");
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return batch_err(LBM_ERR_CUDA, "cudaGetDevice failed");
+    }
+    b->max = max_lattices;
+    b->alloc = g_alloc;
+    b->release = g_free;
+    b->alloc_ctx = g_alloc_ctx;
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+    const size_t table = ((size_t)max_lattices * sizeof(BatchEntry<double>) + 255) / 256 * 256;
+    const size_t bytes = table + (size_t)max_lattices * sizeof(int);
+    void *mem = nullptr;
+    if (e == cudaSuccess) {
+        if (b->alloc) {
+            mem = b->alloc(bytes, b->alloc_ctx);
+        } else if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            mem = nullptr;
+        }
+    }
+    if (e != cudaSuccess || !mem) {
+        lbm_batch_destroy(b);
+        return batch_err(e != cudaSuccess ? LBM_ERR_CUDA : LBM_ERR_OOM, "lbm_batch_create: setup failed");
+    }
+    b->entries = mem;
+    b->parity = reinterpret_cast<int *>(static_cast<char *>(mem) + table);
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_add(lbm_batch b, lbm_handle h) {
+    if (!b || !h) return batch_err(LBM_ERR_ARG, "lbm_batch_add: NULL argument");
+    if (!h->params_set) return batch_err(LBM_ERR_STATE, "lbm_batch_add: lattice has no parameters");
+    if (h->device != b->device) return batch_err(LBM_ERR_ARG, "lbm_batch_add: lattice on another device");
+    for (lbm_s *m : b->members)
+        if (m == h) return batch_err(LBM_ERR_ARG, "lbm_batch_add: lattice already in the batch");
+    if ((int)b->members.size() >= b->max) return batch_err(LBM_ERR_ARG, "lbm_batch_add: batch is full");
+    if (!b->members.empty() &&
+        (h->precision != b->precision || h->p.problem != b->problem || (h->p.flow_on != 0) != (b->flow != 0)))
+        return batch_err(LBM_ERR_ARG,
+                         "lbm_batch_add: every lattice of a batch needs the same precision, problem and flow_on");
+    if (b->members.empty()) {
+        b->precision = h->precision;
+        b->problem = h->p.problem;
+        b->flow = h->p.flow_on != 0;
+    }
+    b->members.push_back(h);
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_remove(lbm_batch b, lbm_handle h) {
+    if (!b || !h) return batch_err(LBM_ERR_ARG, "lbm_batch_remove: NULL argument");
+    for (size_t r = 0; r < b->members.size(); ++r) {
+        if (b->members[r] == h) {
+            // work queued by the batch on this lattice must finish before the
+            // caller uses it on its own stream
+            DeviceGuard g(b->device);
+            BATCH_TRY(cudaEventRecord(b->ev, b->stream));
+            BATCH_TRY(cudaStreamWaitEvent(h->stream, b->ev, 0));
+            b->members.erase(b->members.begin() + (long)r);
+            b->dirty = true;
+            return LBM_OK;
+        }
+    }
+    return batch_err(LBM_ERR_ARG, "lbm_batch_remove: lattice not in the batch");
+}
+
+int lbm_batch_count(lbm_batch b, int *count) {
+    if (!b || !count) return batch_err(LBM_ERR_ARG, "lbm_batch_count: NULL argument");
+    *count = (int)b->members.size();
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, long long n) {
+    if (!b || n < 0) return batch_err(LBM_ERR_ARG, "lbm_batch_step: bad argument");
+    if (n == 0 || b->members.empty()) return LBM_OK;
+    DeviceGuard g(b->device);
+    // order the batch after everything already queued on the members' streams
+    cudaStream_t last = nullptr;
+    for (lbm_s *h : b->members) {
+        if (h->stream == b->stream || h->stream == last) continue;
+        BATCH_TRY(cudaEventRecord(b->ev, h->stream));
+        BATCH_TRY(cudaStreamWaitEvent(b->stream, b->ev, 0));
+        last = h->stream;
+    }
+    const int rc = by_precision(b->precision, [&](auto t) { return BTRIRT_T(t, batch_steps)(b, n); });
+    if (rc != LBM_OK) return rc;
+    // and the members' streams after the batch
+    BATCH_TRY(cudaEventRecord(b->ev, b->stream));
+    last = nullptr;
+    for (lbm_s *h : b->members) {
+        if (h->stream == b->stream || h->stream == last) continue;
+        BATCH_TRY(cudaStreamWaitEvent(h->stream, b->ev, 0));
+        last = h->stream;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch b) {
+    if (!b) return LBM_OK;
+    DeviceGuard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    batch_free(b, b->entries);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
 // ---------------------------------------------------------------------------
 // lbm_step_static: one diagnostic sweep on caller-owned buffers, with no
 // allocation.  Its reduction scratch (per-block partials, tickets, the FP64

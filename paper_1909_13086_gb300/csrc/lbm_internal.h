@@ -99,6 +99,22 @@ cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim
 template <typename real, typename S>
 cudaError_t launch_fields0(const SweepArgs<real> &a, bool flow, dim3 grid, dim3 block,
                            cudaStream_t s);
+// One lattice of a batch launch: its arguments for both buffer parities and
+// its place in the launch's block numbering.
+template <typename real>
+struct BatchEntry {
+    SweepArgs<real> a[2];  // [p]: source buffer p, destination buffer 1 - p
+    int start;             // first block of this lattice in the launch
+    int gx, gy;            // tile columns and row bands
+    int pad;
+};
+
+// One step of a batch: `entries` points at n device BatchEntry<real> records
+// whose blocks, nblocks in all, run in one launch; parity[r] is entry r's
+// source buffer at step j = 0.  diag: diagnostic sweep plus the per-entry fold.
+template <typename real, typename S>
+cudaError_t launch_batch(const void *entries, const int *parity, int n, int nblocks, int problem,
+                         bool flow, bool diag, int j, cudaStream_t s);
 // Tile-major buffer <-> plane-major FP64 staging (18 planes of nx*ny, f then g).
 // to_staging = true packs buf into stage; false unpacks stage into buf (and,
 // if buf2 is non-NULL, the f planes into buf2 as well).  Values in the staging

@@ -425,7 +425,7 @@ __device__ __forceinline__ double dec_max(double v) { return v; }
 // the thread's sums in the working precision.
 template <typename real>
 __device__ __forceinline__ void diag_partial(real sfl, real sH, real umax2, bool bad, double *dpart,
-                                             double *sh) {
+                                             size_t bid, double *sh) {
     using A = typename DiagAcc<real>::T;
     const real wfl = warp_sum(sfl), wH = warp_sum(sH), wu = warp_max(umax2);
     const int wbad = __any_sync(0xffffffffu, bad) ? 1 : 0;
@@ -433,7 +433,7 @@ __device__ __forceinline__ void diag_partial(real sfl, real sH, real umax2, bool
     const int kind[4] = {0, 0, 1, 1};
     block_fold<4, A>(v, kind, sh);
     if (threadIdx.x == 0) {
-        A *d = reinterpret_cast<A *>(dpart) + 4 * (blockIdx.x + (size_t)blockIdx.y * gridDim.x);
+        A *d = reinterpret_cast<A *>(dpart) + 4 * bid;
 #pragma unroll
         for (int k = 0; k < 4; ++k) d[k] = v[k];
     }
@@ -507,27 +507,26 @@ __device__ __forceinline__ void prefetch_tile_row_l2(const E *p) {
 }
 
 // ---- the sweep ----
+// One block's work: the tile column bx (kTW cells) and the row band by
+// (a.rows rows) of the lattice described by a; gx is the number of tile
+// columns (for the block's partial-sum slot).  Called by lattice_kernel (one
+// lattice, bx = blockIdx.x) and batch_kernel (a block of a batch of lattices).
 template <typename real, typename S, int PROB, bool FLOW, int MODE>
-// FP32 arithmetic: at least 8 blocks of 128 threads per SM (registers capped at
-// 64, the occupancy the memory pipeline needs); FP64 is ALU-bound and keeps its
-// registers.
-__global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
-    lattice_kernel(const SweepArgs<real> a) {
+__device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int bx, const int by,
+                                            const int gx, double *sh) {
     using E = typename Store<S>::elem;
     const E *src = static_cast<const E *>(a.src);
-    __shared__ double sh[32 * 4];
     const int lx = threadIdx.x;
-    const int x = blockIdx.x * kTW + lx;
-    const int y0 = blockIdx.y * a.rows;
+    const int x = bx * kTW + lx;
+    const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
     // Blocks are scheduled roughly in row order, so the row `prefetch` rows
     // ahead belongs to a block that starts a little later: fetching it into L2
     // now shortens that block's load latency.
     if (a.prefetch > 0 && threadIdx.x == 0 && y0 + a.prefetch < a.ny)
-        prefetch_tile_row_l2(src + pop_index(blockIdx.x * kTW, y0 + a.prefetch, 0, a.ny));
+        prefetch_tile_row_l2(src + pop_index(bx * kTW, y0 + a.prefetch, 0, a.ny));
     // the device-side step counter (read by the diagnostics fold after this launch)
-    if (MODE != kFields && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0)
-        a.rec->counter += 1.0;
+    if (MODE != kFields && threadIdx.x == 0 && bx == 0 && by == 0) a.rec->counter += 1.0;
     // Stochastic rounding seed of this step: read from the word of the source
     // buffer's parity; block (0, 0) hands the next value to the other word,
     // which only the next step reads -- no race, and graph replays see a new
@@ -535,12 +534,12 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     uint32_t step_seed = 0;
     if (Store<S>::kSR && MODE != kFields) {
         const double sd = a.rec->rng[a.parity];
-        if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) a.rec->rng[a.parity ^ 1] = sd + 1.0;
+        if (threadIdx.x == 0 && bx == 0 && by == 0) a.rec->rng[a.parity ^ 1] = sd + 1.0;
         step_seed = hash32((uint32_t)(unsigned long long)sd ^ 0x5bd1e995u);
     }
     const bool active = x < a.nx;
     // the warp's 32 columns are clear of both side walls (warp-uniform)
-    const int xw = blockIdx.x * kTW + (lx & ~31);
+    const int xw = bx * kTW + (lx & ~31);
     const bool fastcol = xw >= 1 && xw + 31 <= a.nx - 2;
 
     long long i0 = 0, iL = 0, iR = 0;
@@ -598,14 +597,14 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     if (MODE == kFields) return;
 
     // ---- heated-wall inflow of this step (blocks touching the T_h wall) ----
-    const bool qblock = (PROB == kCavity) ? (a.strip_on && blockIdx.y == 0) : (blockIdx.x == 0);
+    const bool qblock = (PROB == kCavity) ? (a.strip_on && by == 0) : (bx == 0);
     if (qblock) {
         const int kind[1] = {0};
         double v[1] = {warp_sum((double)q)};
         block_fold<1>(v, kind, sh);
         __shared__ bool qlast;
         if (threadIdx.x == 0) {
-            const int slot = (PROB == kCavity) ? blockIdx.x : blockIdx.y;
+            const int slot = (PROB == kCavity) ? bx : by;
             a.qpart[slot] = v[0];
             __threadfence();
             qlast = atomicAdd(a.qcount, 1u) == (unsigned)a.nq - 1u;
@@ -627,7 +626,91 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
 
     // ---- diagnostics: sums within the warp in the working precision (32
     // threads x `rows` cells), then FP64 across warps and blocks ----
-    if (MODE == kSweepDiag) diag_partial<real>(sfl, sH, umax2, bad, a.dpart, sh);
+    if (MODE == kSweepDiag)
+        diag_partial<real>(sfl, sH, umax2, bad, a.dpart, (size_t)bx + (size_t)by * gx, sh);
+}
+
+// FP32 arithmetic: at least 8 blocks of 128 threads per SM (registers capped at
+// 64, the occupancy the memory pipeline needs); FP64 is ALU-bound and keeps its
+// registers.
+template <typename real, typename S, int PROB, bool FLOW, int MODE>
+__global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
+    lattice_kernel(const SweepArgs<real> a) {
+    __shared__ double sh[32 * 4];
+    sweep_block<real, S, PROB, FLOW, MODE>(a, blockIdx.x, blockIdx.y, gridDim.x, sh);
+}
+
+// ---- batches: many lattices of one precision and problem kind per launch ----
+// Block b of a batch launch belongs to the entry r with start[r] <= b <
+// start[r + 1]; within it, local block l = b - start[r] is tile column l % gx,
+// row band l / gx.  Each entry holds the lattice's arguments for both buffer
+// parities; the launch for step j of a chunk uses parity parity[r] ^ (j & 1).
+// The entry's arguments are staged in shared memory once per block.
+template <typename real>
+__device__ __forceinline__ int batch_find(const BatchEntry<real> *e, int n, int b) {
+    int lo = 0, hi = n - 1;  // last entry with start <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&e[mid].start) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename real, typename S, int PROB, bool FLOW, int MODE>
+__global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
+    batch_kernel(const BatchEntry<real> *entries, const int *parity, int n, int j) {
+    __shared__ double sh[32 * 4];
+    __shared__ __align__(16) unsigned char args_sh[sizeof(SweepArgs<real>)];
+    __shared__ int meta[3];
+    if (threadIdx.x == 0) {
+        const int r = batch_find(entries, n, blockIdx.x);
+        const int p = __ldg(parity + r) ^ (j & 1);
+        const int l = blockIdx.x - __ldg(&entries[r].start);
+        const int gx = __ldg(&entries[r].gx);
+        meta[0] = l % gx;
+        meta[1] = l / gx;
+        meta[2] = gx;
+        // stage the arguments of (r, p)
+        const int4 *s4 = reinterpret_cast<const int4 *>(&entries[r].a[p]);
+        int4 *d4 = reinterpret_cast<int4 *>(args_sh);
+        for (unsigned k = 0; k < sizeof(SweepArgs<real>) / 16; ++k) d4[k] = __ldg(s4 + k);
+    }
+    __syncthreads();
+    const SweepArgs<real> &a = *reinterpret_cast<const SweepArgs<real> *>(args_sh);
+    sweep_block<real, S, PROB, FLOW, MODE>(a, meta[0], meta[1], meta[2], sh);
+}
+
+// Per-entry diagnostics fold after a diagnostic batch step: block r folds the
+// gx * gy partials of entry r (thread t: partials t, t + T, ... in order, then
+// a fixed tree) into that lattice's record.
+template <typename real, typename A>
+__global__ void __launch_bounds__(kReduceThreads)
+    batch_diag_reduce_kernel(const BatchEntry<real> *entries) {
+    __shared__ double sh[32 * 4];
+    const int kind[4] = {0, 0, 1, 1};
+    const BatchEntry<real> &e = entries[blockIdx.x];
+    const SweepArgs<real> &a = e.a[0];
+    const unsigned nblk = (unsigned)e.gx * (unsigned)e.gy;
+    A acc[4] = {A(0), A(0), A(0), A(0)};
+    const A *part = reinterpret_cast<const A *>(a.dpart);
+    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) {
+        acc[0] += part[4 * (size_t)b + 0];
+        acc[1] += part[4 * (size_t)b + 1];
+        acc[2] = max(acc[2], part[4 * (size_t)b + 2]);
+        acc[3] = max(acc[3], part[4 * (size_t)b + 3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
+    block_fold<4, A>(acc, kind, sh);
+    if (threadIdx.x == 0) {
+        DevRecord *rec = a.rec;
+        rec->step = rec->counter;
+        rec->melt_sum = dec_sum(acc[0]);
+        rec->H_sum = dec_sum(acc[1]);
+        rec->max_u = dec_max(acc[2]);
+        rec->nan_flag = acc[3] != A(0) ? 1.0 : 0.0;
+        rec->valid = 1.0;
+    }
 }
 
 // SplitMix64 output function (Steele, Lea & Flood 2014; Vigna's public-domain
@@ -677,7 +760,7 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             bad |= !isfinite(H);
         }
     }
-    diag_partial<real>(sfl, sH, real(0), bad, a.dpart, sh);
+    diag_partial<real>(sfl, sH, real(0), bad, a.dpart, blockIdx.x + (size_t)blockIdx.y * gridDim.x, sh);
 }
 
 // Fields of the step-0 state (no streaming; u = 0 by definition).
@@ -783,6 +866,30 @@ cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int
 }
 
 template <typename real, typename S>
+cudaError_t launch_batch(const void *entries, const int *parity, int n, int nblocks, int problem,
+                         bool flow, bool diag, int j, cudaStream_t s) {
+    const BatchEntry<real> *e = static_cast<const BatchEntry<real> *>(entries);
+    const dim3 grid(nblocks), block(kTW);
+#define BTRIRT_BATCH(PROB, FLOW)                                                                 \
+    if (diag)                                                                                    \
+        batch_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(e, parity, n, j);   \
+    else                                                                                         \
+        batch_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(e, parity, n, j);
+    if (problem == kCavity) {
+        if (flow) { BTRIRT_BATCH(kCavity, true) } else { BTRIRT_BATCH(kCavity, false) }
+    } else {
+        if (flow) { BTRIRT_BATCH(kStefan, true) } else { BTRIRT_BATCH(kStefan, false) }
+    }
+#undef BTRIRT_BATCH
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && diag) {
+        batch_diag_reduce_kernel<real, typename DiagAcc<real>::T><<<n, kReduceThreads, 0, s>>>(e);
+        err = cudaGetLastError();
+    }
+    return err;
+}
+
+template <typename real, typename S>
 cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim3 grid,
                         dim3 block, cudaStream_t s) {
     init_kernel<real, S><<<grid, block, 0, s>>>(a, amp, seed);
@@ -817,6 +924,8 @@ cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, 
                                               dim3, cudaStream_t);                               \
     template cudaError_t launch_fields0<REAL, S>(const SweepArgs<REAL> &, bool, dim3, dim3,      \
                                                  cudaStream_t);                                  \
-    template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t);
+    template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t); \
+    template cudaError_t launch_batch<REAL, S>(const void *, const int *, int, int, int, bool, bool, \
+                                               int, cudaStream_t);
 
 }  // namespace btrirt

@@ -65,7 +65,9 @@ class lbm_diag(ctypes.Structure):
 EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_set_diag_every",
             "lbm_set_launch",
             "lbm_read_fields", "lbm_diagnostics", "lbm_read_populations", "lbm_write_populations",
-            "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static")
+            "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
+            "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
+            "lbm_batch_step", "lbm_batch_destroy")
 
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
@@ -98,6 +100,12 @@ def lib() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, ctypes.c_void_p]
     L.lbm_version.restype = ctypes.c_char_p
+    L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.lbm_batch_add.argtypes = [ctypes.c_void_p, H]
+    L.lbm_batch_remove.argtypes = [ctypes.c_void_p, H]
+    L.lbm_batch_count.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    L.lbm_batch_step.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+    L.lbm_batch_destroy.argtypes = [ctypes.c_void_p]
     L.lbm_step_static.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(lbm_params), ctypes.c_longlong,
                                   ctypes.c_void_p, ctypes.POINTER(lbm_diag)]
@@ -198,6 +206,34 @@ def lbm_step_static(src_ptr: int, dst_ptr: int, nx: int, ny: int, precision: int
     return {n: getattr(d, n) for n, _ in lbm_diag._fields_} if want_diag else None
 
 
+def lbm_batch_create(max_lattices: int, stream: int | None = None):
+    b = ctypes.c_void_p()
+    _check(lib().lbm_batch_create(int(max_lattices), ctypes.c_void_p(stream or 0), ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_add(b, h) -> None:
+    _check(lib().lbm_batch_add(b, h))
+
+
+def lbm_batch_remove(b, h) -> None:
+    _check(lib().lbm_batch_remove(b, h))
+
+
+def lbm_batch_count(b) -> int:
+    c = ctypes.c_int()
+    _check(lib().lbm_batch_count(b, ctypes.byref(c)))
+    return c.value
+
+
+def lbm_batch_step(b, n: int) -> None:
+    _check(lib().lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_destroy(b) -> None:
+    _check(lib().lbm_batch_destroy(b))
+
+
 def lbm_destroy(h) -> None:
     _check(lib().lbm_destroy(h))
 
@@ -275,3 +311,33 @@ class Lattice:
     def set_populations(self, f: np.ndarray, g: np.ndarray, step: int = 0):
         lbm_write_populations(self.h, np.ascontiguousarray(f, np.float64),
                               np.ascontiguousarray(g, np.float64), step)
+
+
+class Batch:
+    """Lattices advanced together by one fused launch per step."""
+
+    def __init__(self, max_lattices: int = 64, stream: int | None = None):
+        self.b = lbm_batch_create(max_lattices, stream)
+        self.members = []
+
+    def add(self, lat: Lattice):
+        lbm_batch_add(self.b, lat.h)
+        self.members.append(lat)
+
+    def remove(self, lat: Lattice):
+        lbm_batch_remove(self.b, lat.h)
+        self.members.remove(lat)
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.b, n)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

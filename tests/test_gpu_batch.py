@@ -1,0 +1,97 @@
+"""Batched stepping: lattices advanced together by one fused launch per step
+must end bitwise where they end when stepped alone, whatever else is in the
+batch, through membership changes, graph-replayed chunks and odd step counts."""
+import numpy as np
+import pytest
+
+from paper_1909_13086_gb300 import lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+_STREAMS = []
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    _STREAMS.append(s)
+    return s.cuda_stream
+
+
+CASES = [  # uneven grids, strip positions and Rayleigh numbers
+    (256, 128, dict(Ra=1e6, strip_center=0.2)),
+    (300, 77, dict(Ra=1e5, strip_center=0.65)),
+    (64, 32, dict()),
+    (130, 70, dict(Ra=1e7, strip_center=0.5, strip_width=0.4, seed=9)),
+]
+
+
+def make(stream, prec, nx, ny, kw):
+    return lbm.Lattice(nx, ny, workloads.params(**kw), precision=prec, stream=stream)
+
+
+def state(lat):
+    f, g, step = lat.populations()
+    return f, g, step, lat.diagnostics()
+
+
+def assert_same(a, b):
+    fa, ga, sa, da = a
+    fb, gb, sb, db = b
+    assert sa == sb
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert da == db
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16sr", "bf16"])
+def test_batch_equals_solo(stream, prec):
+    solo = [make(stream, prec, nx, ny, kw) for nx, ny, kw in CASES]
+    for lat in solo:
+        lat.step(150)
+        lat.step(37)
+    members = [make(stream, prec, nx, ny, kw) for nx, ny, kw in CASES]
+    b = lbm.Batch(8, stream)
+    for lat in members:
+        b.add(lat)
+    b.step(150)  # two graph-replayed chunks of 64 and 22 direct steps
+    b.step(37)   # odd: every member's buffer parity flips
+    for s, m in zip(solo, members):
+        assert_same(state(s), state(m))
+
+
+def test_batch_membership_changes(stream):
+    prec = "fp32"
+    a, c, d = (make(stream, prec, *CASES[k][:2], CASES[k][2]) for k in (0, 1, 2))
+    b = lbm.Batch(4, stream)
+    b.add(a)
+    b.add(c)
+    b.step(100)
+    b.add(d)            # joins mid-run
+    b.step(71)
+    b.remove(a)         # leaves; stepped alone afterwards
+    a.step(13)
+    b.step(129)
+    assert lbm.lbm_batch_count(b.b) == 2
+    ref_a = make(stream, prec, *CASES[0][:2], CASES[0][2])
+    ref_a.step(184)
+    ref_c = make(stream, prec, *CASES[1][:2], CASES[1][2])
+    ref_c.step(300)
+    ref_d = make(stream, prec, *CASES[2][:2], CASES[2][2])
+    ref_d.step(200)
+    for ref, got in ((ref_a, a), (ref_c, c), (ref_d, d)):
+        assert_same(state(ref), state(got))
+
+
+def test_batch_rejects_mixed_members(stream):
+    b = lbm.Batch(2, stream)
+    b.add(make(stream, "fp32", 64, 32, {}))
+    with pytest.raises(lbm.LbmError):
+        b.add(make(stream, "fp64", 64, 32, {}))
+    with pytest.raises(lbm.LbmError):
+        b.add(lbm.Lattice(128, 4, workloads.stefan_1024x4(nx=128)[2], stream=stream))
+    b.add(make(stream, "fp32", 70, 40, {}))
+    with pytest.raises(lbm.LbmError):
+        b.add(make(stream, "fp32", 64, 32, {}))  # full
