@@ -156,6 +156,19 @@ int lbm_set_diag_every(lbm_handle h, long long k);
  * diagnostics.  Errors: LBM_ERR_ARG. */
 int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int graph_chunk);
 
+/* Autotuner: times every launch shape of a small candidate set (rows per block
+ * 1, 2, 4; prefetch distance 0, 2, 4, 8, 16, 32 rows) for steps_per_trial
+ * steps each (best of two, after a warm-up) on a scratch lattice with the
+ * handle's size, precision and parameters -- the handle's own state is not
+ * touched, but the scratch lattice is allocated and freed -- and applies the
+ * fastest with lbm_set_launch (graph_chunk unchanged).  The choice is cached
+ * per (nx, ny, precision, problem, flow_on) for the life of the process, so
+ * later handles of the same kind are tuned without timing.  Outputs (may be
+ * NULL): the chosen rows and prefetch, and its time per step in microseconds
+ * (0 when it came from the cache).  Synchronises.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_STATE, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_autotune(lbm_handle h, int steps_per_trial, int *rows, int *prefetch, float *us_per_step);
+
 /* Bit mask selecting the fields of lbm_read_fields. */
 enum { LBM_FIELD_H = 1, LBM_FIELD_T = 2, LBM_FIELD_FL = 4, LBM_FIELD_UX = 8,
        LBM_FIELD_UY = 16, LBM_FIELD_RHO = 32, LBM_FIELD_ALL = 63 };

@@ -663,6 +663,98 @@ const char *lbm_version(void) { return "btrirt 0.1 sm_103a"; }
 
 
 // ---------------------------------------------------------------------------
+// Autotuner: picks the launch shape (rows per block, L2 prefetch distance) for
+// a lattice size by timing candidates on a scratch lattice of the same size,
+// precision and parameters, so the caller's state is untouched.  Results are
+// cached per (nx, ny, precision, problem, flow_on) for the process.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneKey {
+    int nx, ny, precision, problem, flow;
+    bool operator==(const TuneKey &o) const {
+        return nx == o.nx && ny == o.ny && precision == o.precision && problem == o.problem && flow == o.flow;
+    }
+};
+struct TuneEntry {
+    TuneKey key;
+    int rows, prefetch;
+    float us_per_step;
+};
+std::mutex g_tune_mutex;
+std::vector<TuneEntry> g_tune_cache;
+
+}  // namespace
+
+extern "C" int lbm_autotune(lbm_handle h, int steps_per_trial, int *rows_out, int *prefetch_out,
+                            float *us_per_step_out) {
+    if (!h || steps_per_trial < 1) return set_err(h, LBM_ERR_ARG, "lbm_autotune: bad argument");
+    if (!h->params_set) return set_err(h, LBM_ERR_STATE, "lbm_autotune: parameters not set");
+    const TuneKey key{h->nx, h->ny, h->precision, h->p.problem, h->p.flow_on != 0};
+    TuneEntry best{key, h->rows, h->prefetch, 0.0f};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (const TuneEntry &e : g_tune_cache)
+            if (e.key == key) {
+                best = e;
+                cached = true;
+            }
+    }
+    if (!cached) {
+        DeviceGuard g(h->device);
+        lbm_handle t = nullptr;
+        int rc = lbm_create(h->nx, h->ny, h->precision, h->stream, &t);
+        if (rc != LBM_OK) return set_err(h, rc, "lbm_autotune: scratch lattice: %s", lbm_last_error(nullptr));
+        rc = lbm_set_params(t, &h->p);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+            rc = set_err(h, LBM_ERR_CUDA, "lbm_autotune: cudaEventCreate failed");
+        best.us_per_step = 1e30f;
+        const int rows_c[] = {1, 2, 4};
+        const int pf_c[] = {0, 2, 4, 8, 16, 32};
+        for (int rows : rows_c) {
+            if (rc != LBM_OK || rows > h->ny) break;
+            for (int pf : pf_c) {
+                if (rc != LBM_OK) break;
+                if (pf >= h->ny) continue;
+                rc = lbm_set_launch(t, rows, pf, h->graph_chunk);
+                if (rc == LBM_OK) rc = lbm_step(t, 4);  // warm-up (and graph capture)
+                float best_ms = 1e30f;
+                for (int rep = 0; rep < 2 && rc == LBM_OK; ++rep) {
+                    if (cudaEventRecord(e0, t->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+                    if (rc == LBM_OK) rc = lbm_step(t, steps_per_trial);
+                    if (rc == LBM_OK && (cudaEventRecord(e1, t->stream) != cudaSuccess ||
+                                         cudaEventSynchronize(e1) != cudaSuccess))
+                        rc = LBM_ERR_CUDA;
+                    float ms = 0.0f;
+                    if (rc == LBM_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms)
+                        best_ms = ms;
+                }
+                const float us = best_ms * 1000.0f / (float)steps_per_trial;
+                if (rc == LBM_OK && us < best.us_per_step) {
+                    best.rows = rows;
+                    best.prefetch = pf;
+                    best.us_per_step = us;
+                }
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        lbm_destroy(t);
+        if (rc != LBM_OK) return set_err(h, rc < 0 ? rc : LBM_ERR_CUDA, "lbm_autotune: trial failed");
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache.push_back(best);
+    }
+    const int rc = lbm_set_launch(h, best.rows, best.prefetch, h->graph_chunk);
+    if (rc != LBM_OK) return rc;
+    if (rows_out) *rows_out = best.rows;
+    if (prefetch_out) *prefetch_out = best.prefetch;
+    if (us_per_step_out) *us_per_step_out = cached ? 0.0f : best.us_per_step;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batches: many lattices advanced by one launch per step.
 // ---------------------------------------------------------------------------
 struct lbm_batch_s {

@@ -67,7 +67,7 @@ EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_
             "lbm_read_fields", "lbm_diagnostics", "lbm_read_populations", "lbm_write_populations",
             "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
-            "lbm_batch_step", "lbm_batch_destroy")
+            "lbm_batch_step", "lbm_batch_destroy", "lbm_autotune")
 
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, ctypes.c_void_p]
     L.lbm_version.restype = ctypes.c_char_p
+    L.lbm_autotune.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_float)]
     L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
     L.lbm_batch_add.argtypes = [ctypes.c_void_p, H]
     L.lbm_batch_remove.argtypes = [ctypes.c_void_p, H]
@@ -204,6 +206,13 @@ def lbm_step_static(src_ptr: int, dst_ptr: int, nx: int, ny: int, precision: int
                                ctypes.byref(d) if want_diag else None)
     _check(rc)
     return {n: getattr(d, n) for n, _ in lbm_diag._fields_} if want_diag else None
+
+
+def lbm_autotune(h, steps_per_trial: int = 200) -> dict:
+    rows, pf, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().lbm_autotune(h, int(steps_per_trial), ctypes.byref(rows), ctypes.byref(pf),
+                              ctypes.byref(us)), h)
+    return {"rows": rows.value, "prefetch": pf.value, "us_per_step": us.value}
 
 
 def lbm_batch_create(max_lattices: int, stream: int | None = None):

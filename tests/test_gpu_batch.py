@@ -95,3 +95,22 @@ def test_batch_rejects_mixed_members(stream):
     b.add(make(stream, "fp32", 70, 40, {}))
     with pytest.raises(lbm.LbmError):
         b.add(make(stream, "fp32", 64, 32, {}))  # full
+
+
+def test_autotune_leaves_state_and_caches(stream):
+    nx, ny, p = 256, 128, workloads.params(Ra=1e6, strip_center=0.35)
+    lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    lat.step(10)
+    before = state(lat)
+    t1 = lbm.lbm_autotune(lat.h, 50)
+    assert t1["rows"] in (1, 2, 4) and t1["prefetch"] in (0, 2, 4, 8, 16, 32)
+    assert t1["us_per_step"] > 0
+    assert_same(before, state(lat))          # the handle's state is untouched
+    other = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    t2 = lbm.lbm_autotune(other.h, 50)
+    assert t2["us_per_step"] == 0.0 and (t2["rows"], t2["prefetch"]) == (t1["rows"], t1["prefetch"])
+    # a tuned lattice computes exactly what an untuned one does
+    ref = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    ref.step(60)
+    lat.step(50)
+    assert_same(state(ref), state(lat))
