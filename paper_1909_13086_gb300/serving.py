@@ -1,0 +1,261 @@
+"""Continuous-batching serving loop for cavity solves.
+
+Requests (grid size, Rayleigh number, heated-strip position, storage precision,
+step budget) arrive as a Poisson stream.  The server keeps every admitted
+request's populations resident on the GPU and advances all of them together:
+one ``Batch`` per storage precision, stepped in quanta of ``quantum`` steps
+(one fused launch per step for every member, graph-replayed).  Between quanta
+it retires finished requests (their diagnostics are read, their memory freed),
+reports a request whose lattice produced a non-finite value as failed without
+disturbing the others, and admits waiting requests while their HBM footprint
+fits the budget -- so requests that arrive while others are on the GPU join as
+memory frees up and their work overlaps on the device.
+
+The baseline serves the same stream one request at a time, FIFO, in plain
+FP32 (``sequential_fp32``).  Both report p50 / p99 time to result (completion
+minus arrival) and aggregate MLUPS (cells x steps of all completed requests
+over the makespan).
+
+This module drives the C ABI only; the arithmetic is the CUDA library's.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import lbm, workloads
+
+GRIDS = ((256, 128), (512, 256), (1024, 512), (2048, 1024))
+RAS = (1e6, 1e7, 1e8)
+CENTERS = (0.2, 0.35, 0.5, 0.65, 0.8)   # strip of width W/4 stays inside the wall
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the stream starts
+    nx: int
+    ny: int
+    Ra: float
+    center: float
+    precision: str          # "fp32", "bf16sr", "fp16sr", ...
+    steps: int
+
+    def params(self) -> dict:
+        return workloads.params(Ra=self.Ra, strip_center=self.center, seed=1000 + self.rid)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    start: float
+    finish: float
+    ok: bool
+    diag: dict
+
+    @property
+    def latency(self) -> float:
+        return self.finish - self.arrival
+
+
+def poisson_stream(n: int, rate_hz: float, seed: int = 7, steps: int = 2000,
+                   precisions=("fp32", "bf16sr"), grids=GRIDS, ras=RAS, centers=CENTERS):
+    """n requests with exponential inter-arrival times (rate_hz per second),
+    grid, Ra, strip centre and precision drawn uniformly (seeded)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_hz)
+        nx, ny = grids[rng.integers(len(grids))]
+        out.append(Request(i, t, int(nx), int(ny), float(ras[rng.integers(len(ras))]),
+                           float(centers[rng.integers(len(centers))]),
+                           str(precisions[rng.integers(len(precisions))]), int(steps)))
+    return out
+
+
+ESIZE = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "fp16sr": 2, "bf16sr": 2}
+
+
+def footprint_bytes(nx: int, ny: int, precision: str) -> int:
+    """Device memory of one lattice: two buffers of 18 planes in 128-cell tiles,
+    plus the per-block reduction scratch."""
+    ntx = -(-nx // 128)
+    pops = 2 * ntx * 128 * ny * 18 * ESIZE[precision]
+    scratch = ntx * ny * 32 + max(ntx, ny) * 8 + 4096
+    return pops + scratch
+
+
+class Server:
+    """Continuous batching over resident lattices."""
+
+    def __init__(self, hbm_budget_bytes: int, quantum: int = 100, max_batch: int = 256,
+                 stream: int | None = None, autotune: bool = False):
+        self.budget = int(hbm_budget_bytes)
+        self.quantum = int(quantum)
+        self.max_batch = max_batch
+        self.stream = stream
+        self.autotune = autotune
+        self.batches: dict[str, lbm.Batch] = {}
+        self.active: dict[int, tuple[Request, lbm.Lattice, float]] = {}
+        self.remaining: dict[int, int] = {}
+        self.used = 0
+
+    def _batch(self, precision: str) -> lbm.Batch:
+        if precision not in self.batches:
+            self.batches[precision] = lbm.Batch(self.max_batch, self.stream)
+        return self.batches[precision]
+
+    def can_admit(self, r: Request) -> bool:
+        fp = footprint_bytes(r.nx, r.ny, r.precision)
+        if fp > self.budget:
+            raise ValueError(f"request {r.rid} needs {fp} B, more than the whole budget")
+        return self.used + fp <= self.budget and len(self.active) < self.max_batch
+
+    def admit(self, r: Request, now: float):
+        lat = lbm.Lattice(r.nx, r.ny, r.params(), precision=r.precision, stream=self.stream)
+        if self.autotune:
+            lbm.lbm_autotune(lat.h, 50)
+        self._batch(r.precision).add(lat)
+        self.active[r.rid] = (r, lat, now)
+        self.remaining[r.rid] = r.steps
+        self.used += footprint_bytes(r.nx, r.ny, r.precision)
+
+    def step_quantum(self):
+        """Advance every active request by one quantum (or less, to land exactly
+        on the smallest remaining budget)."""
+        if not self.active:
+            return 0
+        q = min(self.quantum, min(self.remaining.values()))
+        for b in self.batches.values():
+            b.step(q)
+        for rid in self.remaining:
+            self.remaining[rid] -= q
+        return q
+
+    def retire(self, now_fn) -> list[Result]:
+        """Collect finished requests (and failed ones: a non-finite value in any
+        of their cells) and free their lattices."""
+        done = []
+        for rid in list(self.active):
+            r, lat, start = self.active[rid]
+            finished = self.remaining[rid] <= 0
+            if not finished:
+                continue
+            d = lat.diagnostics(raise_on_diverged=False)
+            done.append(Result(rid, r.arrival, start, now_fn(), d["nan_flag"] == 0, d))
+            self._batch(r.precision).remove(lat)
+            lat.close()
+            del self.active[rid]
+            del self.remaining[rid]
+            self.used -= footprint_bytes(r.nx, r.ny, r.precision)
+        return done
+
+    def close(self):
+        for rid in list(self.active):
+            _, lat, _ = self.active.pop(rid)
+            lat.close()
+        for b in self.batches.values():
+            b.close()
+        self.batches.clear()
+
+
+def serve(requests, hbm_budget_bytes: int, quantum: int = 100, stream: int | None = None,
+          autotune: bool = False, clock=time.perf_counter):
+    """Serve a request stream with continuous batching; arrivals are replayed
+    in real time relative to the start.  Returns (results, makespan_s)."""
+    pending = sorted(requests, key=lambda r: r.arrival)
+    srv = Server(hbm_budget_bytes, quantum, stream=stream, autotune=autotune)
+    t0 = clock()
+    now = lambda: clock() - t0  # noqa: E731
+    results: list[Result] = []
+    i = 0
+    waiting: list[Request] = []
+    try:
+        while i < len(pending) or waiting or srv.active:
+            t = now()
+            while i < len(pending) and pending[i].arrival <= t:
+                waiting.append(pending[i])
+                i += 1
+            # admission by HBM footprint, first come first served
+            while waiting and srv.can_admit(waiting[0]):
+                srv.admit(waiting.pop(0), now())
+            if not srv.active:
+                if i < len(pending):
+                    time.sleep(max(0.0, pending[i].arrival - now()))
+                continue
+            srv.step_quantum()
+            results += srv.retire(now)
+    finally:
+        srv.close()
+    return results, now()
+
+
+def sequential_fp32(requests, stream: int | None = None, clock=time.perf_counter):
+    """Baseline: one request at a time, FIFO, plain FP32 (lbm_step)."""
+    pending = sorted(requests, key=lambda r: r.arrival)
+    t0 = clock()
+    now = lambda: clock() - t0  # noqa: E731
+    results = []
+    for r in pending:
+        if now() < r.arrival:
+            time.sleep(r.arrival - now())
+        start = now()
+        lat = lbm.Lattice(r.nx, r.ny, r.params(), precision="fp32", stream=stream)
+        lat.step(r.steps)
+        d = lat.diagnostics(raise_on_diverged=False)
+        results.append(Result(r.rid, r.arrival, start, now(), d["nan_flag"] == 0, d))
+        lat.close()
+    return results, now()
+
+
+def summarize(results, requests, makespan: float) -> dict:
+    by_id = {r.rid: r for r in requests}
+    lat = np.array([x.latency for x in results])
+    work = sum(by_id[x.rid].cells * by_id[x.rid].steps for x in results)
+    return {"requests": len(results), "failed": int(sum(not x.ok for x in results)),
+            "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "mlups": work / makespan / 1e6 if makespan > 0 else None,
+            "makespan_s": makespan}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="serve a Poisson stream of cavity solves")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=40.0, help="arrivals per second")
+    ap.add_argument("--steps", type=int, default=2000, help="step budget of every request")
+    ap.add_argument("--quantum", type=int, default=100)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--precisions", default="fp32,bf16sr")
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--no-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    import torch
+
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    reqs = poisson_stream(args.requests, args.rate, args.seed, args.steps,
+                          tuple(args.precisions.split(",")))
+    res, mk = serve(reqs, int(args.budget_gb * 2 ** 30), args.quantum, s.cuda_stream)
+    out = {"mode": "continuous batching", **summarize(res, reqs, mk),
+           "precisions": args.precisions, "rate_hz": args.rate, "steps": args.steps}
+    print(json.dumps(out), flush=True)
+    if not args.no_baseline:
+        res_b, mk_b = sequential_fp32(reqs, s.cuda_stream)
+        print(json.dumps({"mode": "sequential fp32", **summarize(res_b, reqs, mk_b)}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

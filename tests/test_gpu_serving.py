@@ -1,0 +1,89 @@
+"""Continuous-batching server: every result is the one the request gets when
+solved alone; admission respects the HBM budget; a failing request does not
+disturb the others."""
+import numpy as np
+import pytest
+
+from paper_1909_13086_gb300 import lbm, serving
+
+pytestmark = pytest.mark.gpu
+
+_STREAMS = []
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    _STREAMS.append(s)
+    return s.cuda_stream
+
+
+def small_stream(n=8, steps=300):
+    return serving.poisson_stream(n, rate_hz=200.0, seed=3, steps=steps,
+                                  precisions=("fp32", "bf16sr", "fp16sr"),
+                                  grids=((256, 128), (512, 256), (300, 77)), ras=(1e5, 1e6, 1e7))
+
+
+def solo(r, stream):
+    lat = lbm.Lattice(r.nx, r.ny, r.params(), precision=r.precision, stream=stream)
+    lat.step(r.steps)
+    d = lat.diagnostics(raise_on_diverged=False)
+    f, g, _ = lat.populations()
+    lat.close()
+    return d, f, g
+
+
+def test_each_result_equals_its_solo_run(stream):
+    reqs = small_stream()
+    results, makespan = serving.serve(reqs, 8 * 2 ** 30, quantum=100, stream=stream)
+    assert len(results) == len(reqs) and all(x.ok for x in results)
+    by_id = {r.rid: r for r in reqs}
+    for x in results:
+        d, _, _ = solo(by_id[x.rid], stream)
+        assert x.diag == d  # bitwise: the batch computes exactly the solo steps
+
+
+def test_admission_respects_hbm_budget(stream, monkeypatch):
+    reqs = small_stream(6, 200)
+    one = max(serving.footprint_bytes(r.nx, r.ny, r.precision) for r in reqs)
+    budget = 2 * one + 1
+    peaks = []
+    orig = serving.Server.admit
+
+    def admit(self, r, now):
+        orig(self, r, now)
+        assert self.used <= self.budget
+        peaks.append(len(self.active))
+
+    monkeypatch.setattr(serving.Server, "admit", admit)
+    results, _ = serving.serve(reqs, budget, quantum=50, stream=stream)
+    assert len(results) == len(reqs)
+    assert max(peaks) <= 2
+
+
+def test_failed_request_is_isolated(stream):
+    reqs = small_stream(2, 200)
+    srv = serving.Server(8 * 2 ** 30, quantum=100, stream=stream)
+    try:
+        for r in reqs:
+            srv.admit(r, 0.0)
+        bad_rid = reqs[0].rid
+        _, lat, _ = srv.active[bad_rid]
+        f, g, step = lat.populations()
+        g[0, 5, 5] = np.nan
+        lat.set_populations(f, g, step)
+        while srv.active:
+            srv.step_quantum()
+            done = srv.retire(lambda: 0.0)
+            for x in done:
+                if x.rid == bad_rid:
+                    assert not x.ok and x.diag["nan_flag"] == 1
+                else:
+                    assert x.ok
+                    d, _, _ = solo(reqs[1], stream)
+                    assert x.diag == d
+    finally:
+        srv.close()
