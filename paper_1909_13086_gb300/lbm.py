@@ -271,6 +271,11 @@ def use_torch_allocator() -> None:
     _check(lib().lbm_set_allocator(_torch_hooks[0], _torch_hooks[1], None))
 
 
+def use_default_allocator() -> None:
+    """Back to cudaMalloc / cudaFree for later lbm_create calls."""
+    _check(lib().lbm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+
+
 # ------------------------------------------------------------ convenience
 class Lattice:
     """One lattice on the current CUDA device.  ``params`` is a dict with the

@@ -2,14 +2,16 @@
 
 Requests (grid size, Rayleigh number, heated-strip position, storage precision,
 step budget) arrive as a Poisson stream.  The server keeps every admitted
-request's populations resident on the GPU and advances all of them together:
-one ``Batch`` per storage precision, stepped in quanta of ``quantum`` steps
-(one fused launch per step for every member, graph-replayed).  Between quanta
-it retires finished requests (their diagnostics are read, their memory freed),
-reports a request whose lattice produced a non-finite value as failed without
-disturbing the others, and admits waiting requests while their HBM footprint
-fits the budget -- so requests that arrive while others are on the GPU join as
-memory frees up and their work overlaps on the device.
+request's populations resident on the GPU.  Requests of one storage precision
+and size class form a group: one ``Batch`` (one fused launch per step for all
+members, graph-replayed) on the group's own CUDA stream, advanced in quanta of
+``quantum`` steps.  Groups run concurrently, so small lattices never wait for
+a large one's step, and the host polls each group's quantum by event: when it
+completes, finished requests are retired (diagnostics read, memory freed), a
+request whose lattice produced a non-finite value is reported as failed
+without disturbing the others, and waiting requests are admitted while their
+HBM footprint fits the budget -- requests that arrive while others are on the
+GPU join as memory frees up, and their work overlaps on the device.
 
 The baseline serves the same stream one request at a time, FIFO, in plain
 FP32 (``sequential_fp32``).  Both report p50 / p99 time to result (completion
@@ -97,86 +99,129 @@ def footprint_bytes(nx: int, ny: int, precision: str) -> int:
     return pops + scratch
 
 
+def size_class(nx: int, ny: int) -> int:
+    """Requests are grouped by size so that small lattices never wait for a
+    large lattice's step: 0 up to 256 x 128 cells, 1 up to 512 x 256, 2 up to
+    1024 x 512, 3 above."""
+    c = nx * ny
+    return 0 if c <= 256 * 128 else (1 if c <= 512 * 256 else (2 if c <= 1024 * 512 else 3))
+
+
+class Group:
+    """One batch of same-precision, same-size-class requests on its own CUDA
+    stream, with at most one quantum in flight."""
+
+    def __init__(self, max_batch: int):
+        import torch
+
+        self.stream = torch.cuda.Stream()
+        self.event = torch.cuda.Event()
+        self.batch = lbm.Batch(max_batch, self.stream.cuda_stream)
+        self.members: dict[int, tuple[Request, lbm.Lattice, float]] = {}
+        self.remaining: dict[int, int] = {}
+        self.inflight = 0  # steps of the quantum in flight (0: idle)
+
+    def close(self):
+        for _, lat, _ in self.members.values():
+            lat.close()
+        self.members.clear()
+        self.batch.close()
+
+
 class Server:
-    """Continuous batching over resident lattices."""
+    """Continuous batching over resident lattices (see the module docstring)."""
 
     def __init__(self, hbm_budget_bytes: int, quantum: int = 100, max_batch: int = 256,
-                 stream: int | None = None, autotune: bool = False):
+                 autotune: bool = False):
         self.budget = int(hbm_budget_bytes)
         self.quantum = int(quantum)
         self.max_batch = max_batch
-        self.stream = stream
         self.autotune = autotune
-        self.batches: dict[str, lbm.Batch] = {}
-        self.active: dict[int, tuple[Request, lbm.Lattice, float]] = {}
-        self.remaining: dict[int, int] = {}
+        self.groups: dict[tuple[str, int], Group] = {}
         self.used = 0
 
-    def _batch(self, precision: str) -> lbm.Batch:
-        if precision not in self.batches:
-            self.batches[precision] = lbm.Batch(self.max_batch, self.stream)
-        return self.batches[precision]
+    @property
+    def active(self) -> int:
+        return sum(len(g.members) for g in self.groups.values())
+
+    def group(self, r: Request) -> Group:
+        key = (r.precision, size_class(r.nx, r.ny))
+        if key not in self.groups:
+            self.groups[key] = Group(self.max_batch)
+        return self.groups[key]
 
     def can_admit(self, r: Request) -> bool:
         fp = footprint_bytes(r.nx, r.ny, r.precision)
         if fp > self.budget:
             raise ValueError(f"request {r.rid} needs {fp} B, more than the whole budget")
-        return self.used + fp <= self.budget and len(self.active) < self.max_batch
+        g = self.groups.get((r.precision, size_class(r.nx, r.ny)))
+        if g is not None and (g.inflight or len(g.members) >= self.max_batch):
+            return False  # membership changes wait for the group's quantum
+        return self.used + fp <= self.budget
 
     def admit(self, r: Request, now: float):
-        lat = lbm.Lattice(r.nx, r.ny, r.params(), precision=r.precision, stream=self.stream)
+        g = self.group(r)
+        lat = lbm.Lattice(r.nx, r.ny, r.params(), precision=r.precision, stream=g.stream.cuda_stream)
         if self.autotune:
             lbm.lbm_autotune(lat.h, 50)
-        self._batch(r.precision).add(lat)
-        self.active[r.rid] = (r, lat, now)
-        self.remaining[r.rid] = r.steps
+        g.batch.add(lat)
+        g.members[r.rid] = (r, lat, now)
+        g.remaining[r.rid] = r.steps
         self.used += footprint_bytes(r.nx, r.ny, r.precision)
 
-    def step_quantum(self):
-        """Advance every active request by one quantum (or less, to land exactly
-        on the smallest remaining budget)."""
-        if not self.active:
-            return 0
-        q = min(self.quantum, min(self.remaining.values()))
-        for b in self.batches.values():
-            b.step(q)
-        for rid in self.remaining:
-            self.remaining[rid] -= q
-        return q
-
-    def retire(self, now_fn) -> list[Result]:
-        """Collect finished requests (and failed ones: a non-finite value in any
-        of their cells) and free their lattices."""
-        done = []
-        for rid in list(self.active):
-            r, lat, start = self.active[rid]
-            finished = self.remaining[rid] <= 0
-            if not finished:
+    def launch(self):
+        """Start a quantum on every idle group that has members (asynchronous)."""
+        for g in self.groups.values():
+            if g.inflight or not g.members:
                 continue
-            d = lat.diagnostics(raise_on_diverged=False)
-            done.append(Result(rid, r.arrival, start, now_fn(), d["nan_flag"] == 0, d))
-            self._batch(r.precision).remove(lat)
-            lat.close()
-            del self.active[rid]
-            del self.remaining[rid]
-            self.used -= footprint_bytes(r.nx, r.ny, r.precision)
+            q = min(self.quantum, min(g.remaining.values()))
+            g.batch.step(q)
+            g.event.record(g.stream)
+            g.inflight = q
+
+    def poll(self, now_fn, block: bool = False) -> list[Result]:
+        """Finish the quanta that completed (all of them when block=True):
+        retire finished requests -- diagnostics read, lattice freed -- and
+        report a request whose lattice holds a non-finite value as failed."""
+        done = []
+        for g in self.groups.values():
+            if not g.inflight:
+                continue
+            if block:
+                g.event.synchronize()
+            elif not g.event.query():
+                continue
+            for rid in g.remaining:
+                g.remaining[rid] -= g.inflight
+            g.inflight = 0
+            for rid in [k for k, v in g.remaining.items() if v <= 0]:
+                r, lat, start = g.members.pop(rid)
+                del g.remaining[rid]
+                d = lat.diagnostics(raise_on_diverged=False)
+                done.append(Result(rid, r.arrival, start, now_fn(), d["nan_flag"] == 0, d))
+                g.batch.remove(lat)
+                lat.close()
+                self.used -= footprint_bytes(r.nx, r.ny, r.precision)
         return done
 
+    def busy(self) -> bool:
+        return any(g.inflight for g in self.groups.values())
+
     def close(self):
-        for rid in list(self.active):
-            _, lat, _ = self.active.pop(rid)
-            lat.close()
-        for b in self.batches.values():
-            b.close()
-        self.batches.clear()
+        for g in self.groups.values():
+            g.close()
+        self.groups.clear()
 
 
-def serve(requests, hbm_budget_bytes: int, quantum: int = 100, stream: int | None = None,
-          autotune: bool = False, clock=time.perf_counter):
+def serve(requests, hbm_budget_bytes: int, quantum: int = 100, autotune: bool = False,
+          clock=time.perf_counter, max_batch: int = 256):
     """Serve a request stream with continuous batching; arrivals are replayed
     in real time relative to the start.  Returns (results, makespan_s)."""
     pending = sorted(requests, key=lambda r: r.arrival)
-    srv = Server(hbm_budget_bytes, quantum, stream=stream, autotune=autotune)
+    # Lattices come and go while other groups run: take their memory from the
+    # caching allocator, since cudaFree would wait for the whole device.
+    lbm.use_torch_allocator()
+    srv = Server(hbm_budget_bytes, quantum, max_batch=max_batch, autotune=autotune)
     t0 = clock()
     now = lambda: clock() - t0  # noqa: E731
     results: list[Result] = []
@@ -188,17 +233,26 @@ def serve(requests, hbm_budget_bytes: int, quantum: int = 100, stream: int | Non
             while i < len(pending) and pending[i].arrival <= t:
                 waiting.append(pending[i])
                 i += 1
-            # admission by HBM footprint, first come first served
-            while waiting and srv.can_admit(waiting[0]):
-                srv.admit(waiting.pop(0), now())
-            if not srv.active:
-                if i < len(pending):
-                    time.sleep(max(0.0, pending[i].arrival - now()))
-                continue
-            srv.step_quantum()
-            results += srv.retire(now)
+            # admission by HBM footprint, first come first served (a request
+            # whose group is mid-quantum waits for it; later ones may pass it)
+            still = []
+            for r in waiting:
+                if srv.can_admit(r):
+                    srv.admit(r, now())
+                else:
+                    still.append(r)
+            waiting = still
+            srv.launch()
+            if srv.busy():
+                got = srv.poll(now)
+                results += got
+                if not got:
+                    time.sleep(20e-6)
+            elif not srv.active and i < len(pending):
+                time.sleep(max(0.0, pending[i].arrival - now()))
     finally:
         srv.close()
+        lbm.use_default_allocator()
     return results, now()
 
 
@@ -248,7 +302,7 @@ def main(argv=None):
     s = torch.cuda.Stream()
     reqs = poisson_stream(args.requests, args.rate, args.seed, args.steps,
                           tuple(args.precisions.split(",")))
-    res, mk = serve(reqs, int(args.budget_gb * 2 ** 30), args.quantum, s.cuda_stream)
+    res, mk = serve(reqs, int(args.budget_gb * 2 ** 30), args.quantum)
     out = {"mode": "continuous batching", **summarize(res, reqs, mk),
            "precisions": args.precisions, "rate_hz": args.rate, "steps": args.steps}
     print(json.dumps(out), flush=True)

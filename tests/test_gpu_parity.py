@@ -299,7 +299,7 @@ def test_torch_allocator_hook(orc, stream):
         lat.close()
         assert torch.cuda.memory_allocated() == before
     finally:
-        lbm.lib().lbm_set_allocator(lbm.ALLOC_FN(), lbm.FREE_FN(), None)
+        lbm.use_default_allocator()
 
 
 # ------------------------------------------------------------ full size

@@ -38,7 +38,7 @@ def solo(r, stream):
 
 def test_each_result_equals_its_solo_run(stream):
     reqs = small_stream()
-    results, makespan = serving.serve(reqs, 8 * 2 ** 30, quantum=100, stream=stream)
+    results, makespan = serving.serve(reqs, 8 * 2 ** 30, quantum=100)
     assert len(results) == len(reqs) and all(x.ok for x in results)
     by_id = {r.rid: r for r in reqs}
     for x in results:
@@ -56,34 +56,39 @@ def test_admission_respects_hbm_budget(stream, monkeypatch):
     def admit(self, r, now):
         orig(self, r, now)
         assert self.used <= self.budget
-        peaks.append(len(self.active))
+        peaks.append(self.active)
 
     monkeypatch.setattr(serving.Server, "admit", admit)
-    results, _ = serving.serve(reqs, budget, quantum=50, stream=stream)
+    results, _ = serving.serve(reqs, budget, quantum=50)
     assert len(results) == len(reqs)
     assert max(peaks) <= 2
 
 
 def test_failed_request_is_isolated(stream):
-    reqs = small_stream(2, 200)
-    srv = serving.Server(8 * 2 ** 30, quantum=100, stream=stream)
+    reqs = small_stream(3, 200)
+    for r in reqs:  # all in one group: same precision and size class
+        r.precision, r.nx, r.ny = "fp32", 256, 128
+    srv = serving.Server(8 * 2 ** 30, quantum=100)
     try:
         for r in reqs:
             srv.admit(r, 0.0)
         bad_rid = reqs[0].rid
-        _, lat, _ = srv.active[bad_rid]
-        f, g, step = lat.populations()
-        g[0, 5, 5] = np.nan
-        lat.set_populations(f, g, step)
+        (g,) = srv.groups.values()
+        _, lat, _ = g.members[bad_rid]
+        f, gg, step = lat.populations()
+        gg[0, 5, 5] = np.nan
+        lat.set_populations(f, gg, step)
+        seen = 0
         while srv.active:
-            srv.step_quantum()
-            done = srv.retire(lambda: 0.0)
-            for x in done:
+            srv.launch()
+            for x in srv.poll(lambda: 0.0, block=True):
+                seen += 1
                 if x.rid == bad_rid:
                     assert not x.ok and x.diag["nan_flag"] == 1
                 else:
                     assert x.ok
-                    d, _, _ = solo(reqs[1], stream)
+                    d, _, _ = solo(next(r for r in reqs if r.rid == x.rid), stream)
                     assert x.diag == d
+        assert seen == 3
     finally:
         srv.close()
