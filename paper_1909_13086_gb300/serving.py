@@ -109,12 +109,15 @@ def size_class(nx: int, ny: int) -> int:
 
 class Group:
     """One batch of same-precision, same-size-class requests on its own CUDA
-    stream, with at most one quantum in flight."""
+    stream, with at most one quantum in flight.  The stream's priority rises as
+    the size class falls: when SMs free up, the block scheduler serves the
+    small lattices first (shortest work first), and the large ones take the
+    rest of the GPU."""
 
-    def __init__(self, max_batch: int):
+    def __init__(self, max_batch: int, size_cls: int = 0):
         import torch
 
-        self.stream = torch.cuda.Stream()
+        self.stream = torch.cuda.Stream(priority=-(3 - size_cls))
         self.event = torch.cuda.Event()
         self.batch = lbm.Batch(max_batch, self.stream.cuda_stream)
         self.members: dict[int, tuple[Request, lbm.Lattice, float]] = {}
@@ -147,7 +150,7 @@ class Server:
     def group(self, r: Request) -> Group:
         key = (r.precision, size_class(r.nx, r.ny))
         if key not in self.groups:
-            self.groups[key] = Group(self.max_batch)
+            self.groups[key] = Group(self.max_batch, key[1])
         return self.groups[key]
 
     def can_admit(self, r: Request) -> bool:

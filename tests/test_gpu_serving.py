@@ -48,7 +48,9 @@ def test_each_result_equals_its_solo_run(stream):
 
 def test_admission_respects_hbm_budget(stream, monkeypatch):
     reqs = small_stream(6, 200)
-    one = max(serving.footprint_bytes(r.nx, r.ny, r.precision) for r in reqs)
+    for r in reqs:  # equal footprints: the budget holds exactly two
+        r.nx, r.ny, r.precision = 256, 128, "fp32"
+    one = serving.footprint_bytes(256, 128, "fp32")
     budget = 2 * one + 1
     peaks = []
     orig = serving.Server.admit
