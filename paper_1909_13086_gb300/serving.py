@@ -134,8 +134,16 @@ class Group:
 class Server:
     """Continuous batching over resident lattices (see the module docstring)."""
 
+    # Lattices of size class c admitted at once.  One 2048 x 1024 lattice fills
+    # the GPU by itself (16,384 blocks), so large requests run one after the
+    # other at full speed instead of sharing the GPU in lockstep -- which would
+    # make an early request finish only with the last one -- while small ones,
+    # far from filling it alone, are batched without limit.
+    CLASS_CAP = {0: 1 << 30, 1: 8, 2: 2, 3: 1}
+
     def __init__(self, hbm_budget_bytes: int, quantum: int = 100, max_batch: int = 256,
-                 autotune: bool = False):
+                 autotune: bool = False, class_cap: dict | None = None):
+        self.class_cap = dict(self.CLASS_CAP if class_cap is None else class_cap)
         self.budget = int(hbm_budget_bytes)
         self.quantum = int(quantum)
         self.max_batch = max_batch
@@ -157,10 +165,12 @@ class Server:
         fp = footprint_bytes(r.nx, r.ny, r.precision)
         if fp > self.budget:
             raise ValueError(f"request {r.rid} needs {fp} B, more than the whole budget")
-        g = self.groups.get((r.precision, size_class(r.nx, r.ny)))
+        cls = size_class(r.nx, r.ny)
+        g = self.groups.get((r.precision, cls))
         if g is not None and (g.inflight or len(g.members) >= self.max_batch):
             return False  # membership changes wait for the group's quantum
-        return self.used + fp <= self.budget
+        in_class = sum(len(h.members) for (_, c), h in self.groups.items() if c == cls)
+        return in_class < self.class_cap[cls] and self.used + fp <= self.budget
 
     def admit(self, r: Request, now: float):
         g = self.group(r)
@@ -217,14 +227,15 @@ class Server:
 
 
 def serve(requests, hbm_budget_bytes: int, quantum: int = 100, autotune: bool = False,
-          clock=time.perf_counter, max_batch: int = 256):
+          clock=time.perf_counter, max_batch: int = 256, class_cap: dict | None = None):
     """Serve a request stream with continuous batching; arrivals are replayed
     in real time relative to the start.  Returns (results, makespan_s)."""
     pending = sorted(requests, key=lambda r: r.arrival)
     # Lattices come and go while other groups run: take their memory from the
     # caching allocator, since cudaFree would wait for the whole device.
     lbm.use_torch_allocator()
-    srv = Server(hbm_budget_bytes, quantum, max_batch=max_batch, autotune=autotune)
+    srv = Server(hbm_budget_bytes, quantum, max_batch=max_batch, autotune=autotune,
+                 class_cap=class_cap)
     t0 = clock()
     now = lambda: clock() - t0  # noqa: E731
     results: list[Result] = []
