@@ -114,10 +114,11 @@ class Group:
     small lattices first (shortest work first), and the large ones take the
     rest of the GPU."""
 
-    def __init__(self, max_batch: int, size_cls: int = 0):
+    def __init__(self, max_batch: int, size_cls: int = 0, policy: str = "small_first"):
         import torch
 
-        self.stream = torch.cuda.Stream(priority=-(3 - size_cls))
+        prio = {"small_first": -(3 - size_cls), "large_first": -size_cls, "equal": 0}[policy]
+        self.stream = torch.cuda.Stream(priority=prio)
         self.event = torch.cuda.Event()
         self.batch = lbm.Batch(max_batch, self.stream.cuda_stream)
         self.members: dict[int, tuple[Request, lbm.Lattice, float]] = {}
@@ -142,8 +143,9 @@ class Server:
     CLASS_CAP = {0: 1 << 30, 1: 8, 2: 2, 3: 1}
 
     def __init__(self, hbm_budget_bytes: int, quantum: int = 100, max_batch: int = 256,
-                 autotune: bool = False, class_cap: dict | None = None):
+                 autotune: bool = False, class_cap: dict | None = None, policy: str = "small_first"):
         self.class_cap = dict(self.CLASS_CAP if class_cap is None else class_cap)
+        self.policy = policy
         self.budget = int(hbm_budget_bytes)
         self.quantum = int(quantum)
         self.max_batch = max_batch
@@ -158,7 +160,7 @@ class Server:
     def group(self, r: Request) -> Group:
         key = (r.precision, size_class(r.nx, r.ny))
         if key not in self.groups:
-            self.groups[key] = Group(self.max_batch, key[1])
+            self.groups[key] = Group(self.max_batch, key[1], self.policy)
         return self.groups[key]
 
     def can_admit(self, r: Request) -> bool:
@@ -227,7 +229,8 @@ class Server:
 
 
 def serve(requests, hbm_budget_bytes: int, quantum: int = 100, autotune: bool = False,
-          clock=time.perf_counter, max_batch: int = 256, class_cap: dict | None = None):
+          clock=time.perf_counter, max_batch: int = 256, class_cap: dict | None = None,
+          policy: str = "small_first"):
     """Serve a request stream with continuous batching; arrivals are replayed
     in real time relative to the start.  Returns (results, makespan_s)."""
     pending = sorted(requests, key=lambda r: r.arrival)
@@ -235,7 +238,7 @@ def serve(requests, hbm_budget_bytes: int, quantum: int = 100, autotune: bool = 
     # caching allocator, since cudaFree would wait for the whole device.
     lbm.use_torch_allocator()
     srv = Server(hbm_budget_bytes, quantum, max_batch=max_batch, autotune=autotune,
-                 class_cap=class_cap)
+                 class_cap=class_cap, policy=policy)
     t0 = clock()
     now = lambda: clock() - t0  # noqa: E731
     results: list[Result] = []
