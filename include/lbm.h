@@ -185,6 +185,20 @@ int lbm_read_fields(lbm_handle h, unsigned mask, double *H, double *T, double *f
  * LBM_ERR_DIVERGED (with *out filled) if nan_flag is set. */
 int lbm_diagnostics(lbm_handle h, lbm_diag *out);
 
+/* History of the run (the melt-fraction and Nusselt histories of Sec. 3.2):
+ * a device ring of `capacity` entries (0 frees it) that every step fills with
+ * its heated-wall inflow Q and every diagnostic step also with its melt
+ * fraction, without any host round trip.  Cleared on (re)allocation. */
+int lbm_set_history(lbm_handle h, long long capacity);
+
+/* Read the newest min(max, capacity) history entries, oldest first: step, Q,
+ * Nu (from Q, as in lbm_diag) and melt fraction (NaN on steps without
+ * diagnostics).  Steps with no entry (a cavity without a heated strip between
+ * diagnostic steps, or overwritten) are skipped.  Any output pointer may be
+ * NULL; *count receives the number of entries.  Synchronises. */
+int lbm_read_history(lbm_handle h, int max, long long *step, double *Q, double *Nu, double *melt,
+                     int *count);
+
 /* Checkpoint: the current post-collision populations (9*nx*ny doubles each
  * for f and g, plane-major) and the step counter.  Synchronises. */
 int lbm_read_populations(lbm_handle h, double *f, double *g, long long *step);

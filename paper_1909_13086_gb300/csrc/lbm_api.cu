@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -77,6 +78,9 @@ struct lbm_s {
     // FP64 staging for field and population read-back / write (18 x nx*ny
     // doubles), allocated on first use
     double *stage = nullptr;
+    // history ring (lbm_set_history): 4 doubles per entry
+    double *hist = nullptr;
+    long long hist_cap = 0;
     // allocator used for this handle's memory
     lbm_alloc_fn alloc = nullptr;
     lbm_free_fn release = nullptr;
@@ -176,6 +180,8 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.dpart2 = h->dpart2;
     a.dticket = h->counters + 1;
     a.rec = h->rec;
+    a.hist = h->hist;
+    a.hist_cap = h->hist_cap;
     a.step = h->step;
     return a;
 }
@@ -632,6 +638,50 @@ int lbm_set_launch(lbm_handle h, int rows, int prefetch_rows, int graph_chunk) {
     return LBM_OK;
 }
 
+int lbm_set_history(lbm_handle h, long long capacity) {
+    if (!h || capacity < 0) return set_err(h, LBM_ERR_ARG, "lbm_set_history: bad argument");
+    DeviceGuard g(h->device);
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    dev_free(h, h->hist);
+    h->hist = nullptr;
+    h->hist_cap = 0;
+    if (capacity == 0) return LBM_OK;
+    h->hist = static_cast<double *>(dev_alloc(h, (size_t)capacity * 4 * sizeof(double)));
+    if (!h->hist) return set_err(h, LBM_ERR_OOM, "lbm_set_history: device allocation failed");
+    h->hist_cap = capacity;
+    // all-ones bytes are NaN doubles: an empty slot has a NaN step
+    CUDA_TRY(h, cudaMemsetAsync(h->hist, 0xff, (size_t)capacity * 4 * sizeof(double), h->stream));
+    return LBM_OK;
+}
+
+int lbm_read_history(lbm_handle h, int max, long long *step, double *Q, double *Nu, double *melt,
+                     int *count) {
+    if (!h || max < 0 || !count) return set_err(h, LBM_ERR_ARG, "lbm_read_history: bad argument");
+    *count = 0;
+    if (!h->hist || max == 0) return LBM_OK;
+    DeviceGuard g(h->device);
+    std::vector<double> ring((size_t)h->hist_cap * 4);
+    CUDA_TRY(h, cudaMemcpyAsync(ring.data(), h->hist, ring.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    // the newest entries, oldest first: slot of step s is s mod capacity
+    const long long last = h->step;
+    const long long first = std::max(0ll, std::max(last - h->hist_cap + 1, last - (long long)max + 1));
+    int n = 0;
+    for (long long s = first; s <= last; ++s) {
+        const double *e = &ring[(size_t)(s % h->hist_cap) * 4];
+        if (!(e[0] == (double)s)) continue;  // slot not written for step s (no heated wall, or not yet)
+        if (step) step[n] = s;
+        if (Q) Q[n] = e[1];
+        if (Nu) Nu[n] = h->d.heated_len > 0.0 ? e[1] * h->d.Href / (h->d.alpha * h->d.heated_len) : 0.0;
+        if (melt) melt[n] = e[2];
+        ++n;
+    }
+    *count = n;
+    return LBM_OK;
+}
+
 int lbm_destroy(lbm_handle h) {
     if (!h) return LBM_OK;
     DeviceGuard g(h->device);
@@ -641,6 +691,7 @@ int lbm_destroy(lbm_handle h) {
     dev_free(h, h->buf[1]);
     dev_free(h, h->scratch);
     dev_free(h, h->stage);
+    dev_free(h, h->hist);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return LBM_OK;

@@ -76,6 +76,10 @@ struct SweepArgs {
     double *dpart2;        // fold kernel: 4 partials per fold block
     unsigned *dticket;     // fold kernel: ticket counter, reset by its last block
     DevRecord *rec;
+    // optional history ring (lbm_set_history): entry k = 4 doubles {step, Q,
+    // melt fraction, unused} for step k mod hist_cap; NULL = off
+    double *hist;
+    long long hist_cap;
     long long step;        // step index the launch produces (host bookkeeping only;
                            // the record takes its step from rec->counter)
     // field outputs (kFields), nx*ny doubles each, row-major; NULL = skip

@@ -452,10 +452,21 @@ __device__ __forceinline__ void load4(A (&acc)[4], const A *part, unsigned idx, 
     for (int k = 0; k < 4; ++k) acc[k] = ok ? __ldcg(part + 4 * (size_t)idx + k) : A(0);
 }
 
+// A full history entry at a diagnostic step: step, this step's heated-wall
+// inflow, melt fraction.
+__device__ __forceinline__ void hist_put(double *hist, long long cap, const DevRecord *rec,
+                                         double ncells) {
+    const long long st = (long long)rec->step;
+    double *e = hist + 4 * (st % cap);
+    e[0] = rec->step;
+    e[1] = rec->Q_last;
+    e[2] = rec->melt_sum / ncells;
+}
+
 template <typename A>
 __global__ void __launch_bounds__(kReduceThreads)
     diag_reduce_kernel(const double *dpart, unsigned nblk, double *part2, unsigned *ticket,
-                       DevRecord *rec, int init) {
+                       DevRecord *rec, int init, double *hist, long long hist_cap, double ncells) {
     __shared__ double sh[32 * 4];
     __shared__ bool last;
     const int kind[4] = {0, 0, 1, 1};
@@ -492,6 +503,7 @@ __global__ void __launch_bounds__(kReduceThreads)
             rec->counter = 0.0;
         }
         *ticket = 0u;
+        if (hist) hist_put(hist, hist_cap, rec, ncells);
     }
 }
 
@@ -620,6 +632,13 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
                 a.rec->Q_last = v[0];
                 a.rec->Q_cum += v[0];
                 *a.qcount = 0u;
+                if (a.hist) {  // this step's inflow; the melt fraction comes with diagnostics
+                    const long long st = (long long)__ldcg(&a.rec->counter);
+                    double *e = a.hist + 4 * (st % a.hist_cap);
+                    e[0] = (double)st;
+                    e[1] = v[0];
+                    e[2] = __longlong_as_double(0x7ff8000000000000ll);
+                }
             }
         }
     }
@@ -710,6 +729,7 @@ __global__ void __launch_bounds__(kReduceThreads)
         rec->max_u = dec_max(acc[2]);
         rec->nan_flag = acc[3] != A(0) ? 1.0 : 0.0;
         rec->valid = 1.0;
+        if (a.hist) hist_put(a.hist, a.hist_cap, rec, (double)a.nx * (double)a.ny);
     }
 }
 
@@ -847,7 +867,8 @@ static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, bool 
     const unsigned nblk = grid.x * grid.y;
     const unsigned nred = (nblk + kReduceThreads - 1) / kReduceThreads;  // <= kReduceThreads
     diag_reduce_kernel<typename DiagAcc<real>::T><<<nred, kReduceThreads, 0, s>>>(
-        a.dpart, nblk, a.dpart2, a.dticket, a.rec, init ? 1 : 0);
+        a.dpart, nblk, a.dpart2, a.dticket, a.rec, init ? 1 : 0, a.hist, a.hist_cap,
+        (double)a.nx * (double)a.ny);
     return cudaGetLastError();
 }
 

@@ -67,7 +67,8 @@ EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_
             "lbm_read_fields", "lbm_diagnostics", "lbm_read_populations", "lbm_write_populations",
             "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
-            "lbm_batch_step", "lbm_batch_destroy", "lbm_autotune")
+            "lbm_batch_step", "lbm_batch_destroy", "lbm_autotune", "lbm_set_history",
+            "lbm_read_history")
 
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
@@ -100,6 +101,9 @@ def lib() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, ctypes.c_void_p]
     L.lbm_version.restype = ctypes.c_char_p
+    L.lbm_set_history.argtypes = [H, ctypes.c_longlong]
+    L.lbm_read_history.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D, _D,
+                                   ctypes.POINTER(ctypes.c_int)]
     L.lbm_autotune.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_float)]
     L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
@@ -206,6 +210,20 @@ def lbm_step_static(src_ptr: int, dst_ptr: int, nx: int, ny: int, precision: int
                                ctypes.byref(d) if want_diag else None)
     _check(rc)
     return {n: getattr(d, n) for n, _ in lbm_diag._fields_} if want_diag else None
+
+
+def lbm_set_history(h, capacity: int) -> None:
+    _check(lib().lbm_set_history(h, int(capacity)), h)
+
+
+def lbm_read_history(h, max_entries: int) -> dict:
+    step = (ctypes.c_longlong * max(1, max_entries))()
+    Q, Nu, melt = (np.empty(max(1, max_entries)) for _ in range(3))
+    n = ctypes.c_int()
+    _check(lib().lbm_read_history(h, int(max_entries), step, _dptr(Q), _dptr(Nu), _dptr(melt),
+                                  ctypes.byref(n)), h)
+    k = n.value
+    return {"step": np.array(step[:k], dtype=np.int64), "Q": Q[:k], "Nu": Nu[:k], "melt": melt[:k]}
 
 
 def lbm_autotune(h, steps_per_trial: int = 200) -> dict:

@@ -114,7 +114,7 @@ class Group:
     small lattices first (shortest work first), and the large ones take the
     rest of the GPU."""
 
-    def __init__(self, max_batch: int, size_cls: int = 0, policy: str = "small_first"):
+    def __init__(self, max_batch: int, size_cls: int = 0, policy: str = "equal"):
         import torch
 
         prio = {"small_first": -(3 - size_cls), "large_first": -size_cls, "equal": 0}[policy]
@@ -143,7 +143,7 @@ class Server:
     CLASS_CAP = {0: 1 << 30, 1: 8, 2: 2, 3: 1}
 
     def __init__(self, hbm_budget_bytes: int, quantum: int = 100, max_batch: int = 256,
-                 autotune: bool = False, class_cap: dict | None = None, policy: str = "small_first"):
+                 autotune: bool = False, class_cap: dict | None = None, policy: str = "equal"):
         self.class_cap = dict(self.CLASS_CAP if class_cap is None else class_cap)
         self.policy = policy
         self.budget = int(hbm_budget_bytes)
@@ -230,7 +230,7 @@ class Server:
 
 def serve(requests, hbm_budget_bytes: int, quantum: int = 100, autotune: bool = False,
           clock=time.perf_counter, max_batch: int = 256, class_cap: dict | None = None,
-          policy: str = "small_first"):
+          policy: str = "equal"):
     """Serve a request stream with continuous batching; arrivals are replayed
     in real time relative to the start.  Returns (results, makespan_s)."""
     pending = sorted(requests, key=lambda r: r.arrival)

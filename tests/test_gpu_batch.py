@@ -118,3 +118,40 @@ def test_autotune_leaves_state_and_caches(stream):
     fl, gl, sl, dl = state(lat)
     assert sr == sl and np.array_equal(fr, fl) and np.array_equal(gr, gl)
     assert dl["melt_fraction"] == pytest.approx(dr["melt_fraction"], rel=1e-6, abs=1e-12)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_history_ring_matches_step_by_step_diagnostics(stream, batched):
+    """The device history (heated-wall inflow every step, melt fraction on the
+    diagnostic steps) equals what step-by-step diagnostics report, also when the
+    steps run as replayed graphs or inside a batch."""
+    nx, ny, p = 200, 90, workloads.params(Ra=1e6, strip_center=0.45)
+    ref = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    want = {}
+    for _ in range(300):
+        ref.step(1)
+        d = ref.diagnostics()
+        want[d["step"]] = (d["Q_strip"], d["Nu"], d["melt_fraction"])
+    lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    lbm.lbm_set_history(lat.h, 512)
+    lbm.lbm_set_diag_every(lat.h, 50)
+    if batched:
+        b = lbm.Batch(2, stream)
+        b.add(lat)
+        b.step(200)  # inside a batch diag_every does not apply: only the last step
+        b.step(100)
+        diag_steps = {200, 300}
+    else:
+        lat.step(300)
+        diag_steps = {50, 100, 150, 200, 250, 300}
+    h = lbm.lbm_read_history(lat.h, 1000)
+    assert list(h["step"]) == list(range(0, 301))
+    for s, q, nu, m in zip(h["step"], h["Q"], h["Nu"], h["melt"]):
+        if s == 0:
+            continue
+        assert q == want[s][0] and nu == pytest.approx(want[s][1], rel=1e-14)
+        if s in diag_steps:
+            assert m == pytest.approx(want[s][2], rel=1e-6, abs=1e-12)
+        else:
+            assert np.isnan(m)
+    assert lbm.lbm_read_history(lat.h, 10)["step"][0] == 291
