@@ -265,11 +265,11 @@ def measure_e2e(args, lat, p, prec, stream, dist, local) -> dict:
     hist = lbm.lbm_read_history(e2e_lat.h, e2e_steps + 1)
     lbm.lbm_read_fields(e2e_lat.h, 63, *[out[k] for k in ("H", "T", "fl", "ux", "uy", "rho")])
     t_e2e = time.perf_counter() - t0
-    assert len(hist["step"]) == e2e_steps + 1
+    assert len(hist["step"]) == e2e_steps
     t_e2e_max, e2e_units = aggregate(t_e2e, float(cells * e2e_steps), dist,
                                      device=torch.device("cuda", local))
     h2d = f_host.nbytes + g_host.nbytes
-    d2h = (e2e_steps + 1) * 32 + sum(a.nbytes for a in out.values())
+    d2h = (e2e_steps + 1) * 32 + sum(a.nbytes for a in out.values())  # the whole ring
     e2e_lat.close()
     return {"value": round(e2e_units / t_e2e_max / 1e6, 1), "unit": METRIC,
             "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),

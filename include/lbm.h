@@ -188,7 +188,8 @@ int lbm_diagnostics(lbm_handle h, lbm_diag *out);
 /* History of the run (the melt-fraction and Nusselt histories of Sec. 3.2):
  * a device ring of `capacity` entries (0 frees it) that every step fills with
  * its heated-wall inflow Q and every diagnostic step also with its melt
- * fraction, without any host round trip.  Cleared on (re)allocation. */
+ * fraction, without any host round trip (steps 1, 2, ...; the initial state
+ * has no entry).  Cleared on (re)allocation. */
 int lbm_set_history(lbm_handle h, long long capacity);
 
 /* Read the newest min(max, capacity) history entries, oldest first: step, Q,

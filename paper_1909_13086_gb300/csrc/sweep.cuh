@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kReduceThreads)
             rec->counter = 0.0;
         }
         *ticket = 0u;
-        if (hist) hist_put(hist, hist_cap, rec, ncells);
+        if (hist && !init) hist_put(hist, hist_cap, rec, ncells);
     }
 }
 

@@ -145,10 +145,8 @@ def test_history_ring_matches_step_by_step_diagnostics(stream, batched):
         lat.step(300)
         diag_steps = {50, 100, 150, 200, 250, 300}
     h = lbm.lbm_read_history(lat.h, 1000)
-    assert list(h["step"]) == list(range(0, 301))
+    assert list(h["step"]) == list(range(1, 301))
     for s, q, nu, m in zip(h["step"], h["Q"], h["Nu"], h["melt"]):
-        if s == 0:
-            continue
         assert q == want[s][0] and nu == pytest.approx(want[s][1], rel=1e-14)
         if s in diag_steps:
             assert m == pytest.approx(want[s][2], rel=1e-6, abs=1e-12)
