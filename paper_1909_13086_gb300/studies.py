@@ -1,0 +1,127 @@
+"""The paper's two studies, run on the GPU through the C ABI.
+
+* ``stefan_k1_sweep`` -- Sec. 3.1 (Figs. 1-2 as numbers): one-phase melting by
+  conduction, T_h = 1, T_m = 0, Ste = 0.01, alpha = 1/6, dx = 1/100, profiles
+  at t = 25, for k1 in {0.1, 0.5, 1.0, 1.5} (k1 = 2.0 has no positive
+  diffusivity, Eq. 5), B-TriRT with k2 = 2 - k1 (Eq. 6) against SRT
+  (k0 = k1 = k2).  Reported per run: the largest temperature error against
+  the Neumann solution (Eqs. 7-8), the largest departure of the solid ahead of
+  the front from T_m, the interface width (cells with 0 < f_l < 1 in a row)
+  and the front position against 2 lambda sqrt(alpha t).
+* ``cavity_location_sweep`` -- Sec. 3.2 (Fig. 3b): the melt-fraction history
+  of the cavity heated from below at Ra 1e8, Pr 6.2, Ste 0.125, D = 0.5 L,
+  512 x 512, for strip centres C = 0.25, 0.375, 0.5 L, up to a given Fourier
+  number (full melting needs ~6.6e7 steps per run at Ma 0.1).
+
+Lattice units (reading of Sec. 3.1's mixed units): dt follows from k1 through
+Eq. 5, dt = dx^2 (1/k1 - 1/2) / (3 alpha), so t = 25 is 25 / dt steps and the
+front X(t) = 2 lambda sqrt(alpha t) becomes X / dx cells.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+
+from . import lbm, workloads
+
+PAPER_STEFAN = dict(Th=1.0, Tm=0.0, Ste=0.01, alpha=1.0 / 6.0, dx=0.01, t=25.0, k1=(0.1, 0.5, 1.0, 1.5))
+
+
+def stefan_lambda(Ste: float) -> float:
+    """Root of Eq. 8, Ste / (exp(l^2) erf(l)) = l sqrt(pi), by bisection."""
+    f = lambda l: l * math.sqrt(math.pi) * math.exp(l * l) * math.erf(l) - Ste  # noqa: E731
+    lo, hi = 0.0, 1.0
+    while f(hi) < 0:
+        hi *= 2
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if f(mid) < 0 else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+def neumann_T(x, t, alpha, lam, Th=1.0, Tm=0.0):
+    """Eq. 7 (x, t in any consistent units)."""
+    X = 2 * lam * math.sqrt(alpha * t)
+    s = 2 * math.sqrt(alpha * t)
+    return np.where(x < X, Th - (Th - Tm) * np.vectorize(math.erf)(x / s) / math.erf(lam), Tm)
+
+
+def stefan_run(k1: float, model: str, nx: int = 100, precision: str = "fp64", stream=None,
+               p=PAPER_STEFAN) -> dict:
+    dx, alpha_phys = p["dx"], p["alpha"]
+    dt = dx * dx * (1.0 / k1 - 0.5) / (3.0 * alpha_phys)
+    steps = int(round(p["t"] / dt))
+    alpha_lu = (1.0 / k1 - 0.5) / 3.0
+    k2 = 2.0 - k1 if model == "btrirt" else k1
+    k0 = 1.0 if model == "btrirt" else k1
+    _, ny, prm = workloads.stefan_1024x4(Ste=p["Ste"], alpha=alpha_lu, k2=k2, k0=k0, nx=nx)
+    lat = lbm.Lattice(nx, ny, prm, precision=precision, stream=stream)
+    lat.step(steps)
+    F = lat.fields(("T", "fl", "H"))
+    T, fl = F["T"][0], F["fl"][0]
+    lam = stefan_lambda(p["Ste"])
+    x = (np.arange(nx) + 0.5) * dx
+    t = steps * dt
+    Tn = neumann_T(x, t, alpha_phys, lam, p["Th"], p["Tm"])
+    X = 2 * lam * math.sqrt(alpha_phys * t)
+    melted = np.nonzero(fl > 1e-12)[0]
+    edge = melted.max() if melted.size else -1
+    ahead = T[edge + 1:]
+    mushy = ((F["fl"] > 1e-12) & (F["fl"] < 1 - 1e-12)).sum(axis=1)
+    d = lat.diagnostics()
+    lat.close()
+    return {"k1": k1, "model": model, "steps": steps,
+            "max_T_error": float(np.abs(T - Tn).max()),
+            "solid_departure_from_Tm": float(np.abs(ahead).max(initial=0.0)),
+            "interface_width_cells": int(mushy.max()),
+            "front_cells": d["front_x"], "front_neumann_cells": X / dx}
+
+
+def stefan_k1_sweep(precision: str = "fp64", stream=None) -> list[dict]:
+    return [stefan_run(k1, m, precision=precision, stream=stream)
+            for k1 in PAPER_STEFAN["k1"] for m in ("btrirt", "srt")]
+
+
+def cavity_location_sweep(fo_end: float = 0.01, n: int = 512, centers=(0.25, 0.375, 0.5),
+                          samples: int = 20, precision: str = "fp32", stream=None) -> dict:
+    """Melt-fraction history at the paper's cavity parameters (Sec. 3.2)."""
+    out = {}
+    for C in centers:
+        p = workloads.params(Ra=1e8, Pr=6.2, Ste=0.125, strip_center=C, strip_width=0.5)
+        lat = lbm.Lattice(n, n, p, precision=precision, stream=stream)
+        alpha = lat.derived()["alpha"]
+        steps_total = int(round(fo_end * n * n / alpha))
+        chunk = max(1, steps_total // samples)
+        hist = []
+        for _ in range(samples):
+            lat.step(chunk)
+            d = lat.diagnostics(raise_on_diverged=False)
+            hist.append((d["step"] * alpha / (n * n), d["melt_fraction"], d["Nu"], d["nan_flag"]))
+        out[C] = hist
+        lat.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="the paper's Stefan and cavity-location studies")
+    ap.add_argument("--study", choices=("stefan", "cavity"), default="stefan")
+    ap.add_argument("--fo", type=float, default=0.01)
+    ap.add_argument("--precision", default=None)
+    args = ap.parse_args(argv)
+    import torch
+
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    if args.study == "stefan":
+        for row in stefan_k1_sweep(args.precision or "fp64", s.cuda_stream):
+            print(json.dumps(row), flush=True)
+    else:
+        res = cavity_location_sweep(args.fo, precision=args.precision or "fp32", stream=s.cuda_stream)
+        print(json.dumps({str(k): v for k, v in res.items()}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
