@@ -169,6 +169,7 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.k1f = (real)h->d.k1f;
     a.k2f = (real)h->d.k2f;
     a.Lh = (real)h->d.Lh;
+    a.inv_Lh = (real)(1.0 / h->d.Lh);
     a.gbeta = (real)h->d.gbeta;
     a.strip_on = h->strip_on;
     a.lo2 = h->lo2;

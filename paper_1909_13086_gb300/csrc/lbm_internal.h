@@ -64,6 +64,7 @@ struct SweepArgs {
     real k0, k1, k2;       // g rates (Eq. 2)
     real k0f, k1f, k2f;    // f rates
     real Lh, gbeta;        // latent heat, g*beta
+    real inv_Lh;           // 1 / Lh
     int strip_on;          // cavity: 1 if the heated segment is non-empty
     int lo2, hi2;          // cavity: crossing heated iff lo2 <= 2x + 1 - c_ix <= hi2
     // heated-wall inflow reduction (every sweep)

@@ -166,7 +166,7 @@ __device__ __forceinline__ uint32_t lcg_next(uint32_t &s) {
 
 // ---- H -> (T, f_l): H_s = C_p T_m = 0, H_l = H_s + L.
 template <typename real>
-__device__ __forceinline__ void invert(real H, real Lh, real &T, real &fl) {
+__device__ __forceinline__ void invert(real H, real Lh, real inv_Lh, real &T, real &fl) {
     if (H <= real(0)) {
         T = H;
         fl = real(0);
@@ -175,9 +175,14 @@ __device__ __forceinline__ void invert(real H, real Lh, real &T, real &fl) {
         fl = real(1);
     } else {
         T = real(0);
-        fl = H / Lh;
+        fl = H * inv_Lh;
     }
 }
+
+// 1 / x: the fast reciprocal in FP32 (about 2 ulp; the FP32 path's tolerance
+// is 1e-5), the exact quotient in FP64 (the parity path).
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // p_i <- a p_i + w_i [B0 + 3 c_i.B1 + 9/2 Q_i:B2]  for all nine directions.
 template <typename real>
@@ -241,13 +246,13 @@ __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, rea
         jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
     }
     m.H = sum9(g);
-    invert(m.H, a.Lh, m.T, m.fl);
+    invert(m.H, a.Lh, a.inv_Lh, m.T, m.fl);
     real Fy = real(0);
     m.ux = real(0);
     m.uy = real(0);
     if (FLOW) {
         Fy = a.gbeta * m.T;
-        const real inv_rho = real(1) / m.rho;
+        const real inv_rho = recip(m.rho);
         m.ux = m.fl * jx * inv_rho;
         m.uy = m.fl * (jy + real(0.5) * Fy) * inv_rho;
     }
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             const double r = (double)(splitmix64(seed ^ cell) >> 11) * 0x1.0p-53;
             const real H = (real)(amp * (2.0 * r - 1.0));
             real T, fl;
-            invert(H, a.Lh, T, fl);
+            invert(H, a.Lh, a.inv_Lh, T, fl);
             const long long c = pop_index(x, y, 0, a.ny);
             // initial state: rounded to nearest
             Store<S>::stg_rn(dst + c + 9 * kTW, H - T + w_of<real>(0) * T);
@@ -804,7 +809,7 @@ __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
             rho = sum9(f);
         }
         real T, fl;
-        invert(H, a.Lh, T, fl);
+        invert(H, a.Lh, a.inv_Lh, T, fl);
         const long long o = (long long)y * a.nx + x;
         if (a.oH) a.oH[o] = (double)H;
         if (a.oT) a.oT[o] = (double)T;
