@@ -70,5 +70,7 @@ def test_argument_errors_need_no_gpu(built):
     assert b"nx and ny" in L.lbm_last_error(None)
     assert L.lbm_create(8, 8, 7, None, ctypes.byref(h)) == built.LBM_ERR_ARG
     assert (built.LBM_FP64, built.LBM_FP32, built.LBM_FP16, built.LBM_BF16) == (0, 1, 2, 3)
+    assert L.lbm_create(8, 65536, 1, None, ctypes.byref(h)) == built.LBM_ERR_ARG   # ny > 65535
+    assert L.lbm_create(65536, 40000, 1, None, ctypes.byref(h)) == built.LBM_ERR_ARG  # > 2^31 cells
     assert L.lbm_step(None, 1) == built.LBM_ERR_ARG
     assert L.lbm_destroy(None) == built.LBM_OK

@@ -480,3 +480,17 @@ def test_16bit_round_to_nearest_stagnates(stream, prec):
         out[pr] = (d["melt_fraction"], abs(d["H_total"] - h0 - d["Q_cum"]) / d["Q_cum"])
     assert out["fp64"][0] - out[prec][0] > 1e-3
     assert out[prec][1] > 1e-2
+
+
+# ------------------------------------------------------------ extreme shapes
+@pytest.mark.parametrize("nx,ny,steps", [(2, 65535, 3), (262144, 2, 3), (129, 65535, 2)])
+def test_extreme_shapes_match_oracle(orc, stream, nx, ny, steps):
+    """The tallest lattice the launch allows (65,535 rows: 65,535 blocks in y),
+    a 2^18-cell-wide strip of 2,048 tiles, and a ragged two-tile width at full
+    height, against the oracle (FP64)."""
+    p = workloads.params(Ra=1e5, init_amp=0.1)
+    ref, lat = run_pair(orc, nx, ny, p, steps, "fp64", stream, threads=8)
+    assert_fields_fp64(lat.fields(), ref.fields())
+    d, dr = lat.diagnostics(), ref.diagnostics()
+    assert d["Q_cum"] == pytest.approx(dr["Q_cum"], rel=1e-12, abs=1e-15)
+    assert d["melt_fraction"] == pytest.approx(dr["melt_fraction"], rel=1e-12, abs=1e-15)
