@@ -38,7 +38,12 @@ BYTES_PER_LUP = {"fp32": 144, "fp64": 288, "fp16": 72, "bf16": 72, "fp16sr": 72,
 DIAG_EVERY = 100
 METRIC = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
-PROFILE = os.path.join(ROOT, "profiles", "sweep_fp32_cavity_2048x1024.md")
+# FP64 operations (adds, subtracts, multiplies, one divide; an FMA counts as
+# two) in one interior-cell update as the sweep writes it out: macroscopic
+# fields 35, g collision 104, f collision 126.
+FP64_FLOPS_PER_LUP = 265
+# GB300 FP64 pipe: 2 FMA per clock per SM, 2 flops each, 152 SMs, 2070 MHz.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_13086_gb300", "csrc", f)
                   for f in ("sweep.cuh", "lbm_internal.h")]
 
@@ -113,11 +118,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic() -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+def profile_path(precision: str) -> str:
+    return os.path.join(ROOT, "profiles", f"sweep_{precision}_cavity_2048x1024.md")
+
+
+def profiled_traffic(precision: str = "fp32") -> float | None:
+    """DRAM bytes per launch of the sweep in `precision` from the committed
+    ncu summary, if it was taken on the current kernel source."""
     try:
-        text = open(PROFILE).read()
+        text = open(profile_path(precision)).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
@@ -330,9 +339,18 @@ def run_ours(args) -> None:
     alg_bytes = BYTES_PER_LUP[prec] * cells
     achieved = alg_bytes / kernel_s / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(prec),
                 "peak_source": f"{peak_kind} HBM copy bandwidth",
                 "algorithmic_bytes_per_launch": alg_bytes}
+    if prec == "fp64":
+        # the FP64 sweep is bound by GB300's FP64 pipe, not by HBM
+        flops = FP64_FLOPS_PER_LUP * cells
+        tflops = flops / kernel_s / 1e12
+        roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                    "traffic": profiled_traffic(prec),
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2070 MHz",
+                    "algorithmic_flops_per_launch": flops, "hbm_achieved_gbs": round(achieved, 1)}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": ws,

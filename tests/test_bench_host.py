@@ -65,10 +65,30 @@ def test_sweep_launch_count():
 def test_profiled_traffic_needs_matching_kernel_hash(tmp_path, monkeypatch):
     prof = tmp_path / "p.md"
     prof.write_text(f"kernel_source_sha256: {bench.kernel_source_hash()}\ndram_bytes_per_launch: 1.5e8\n")
-    monkeypatch.setattr(bench, "PROFILE", str(prof))
+    monkeypatch.setattr(bench, "profile_path", lambda prec: str(prof))
     assert bench.profiled_traffic() == 1.5e8
     prof.write_text("kernel_source_sha256: 0000000000000000\ndram_bytes_per_launch: 1.5e8\n")
     assert bench.profiled_traffic() is None
+
+
+def test_profiled_traffic_is_per_precision(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    h = bench.kernel_source_hash()
+    (tmp_path / "profiles" / "sweep_fp32_cavity_2048x1024.md").write_text(
+        f"kernel_source_sha256: {h}\ndram_bytes_per_launch: 2.5e8\n")
+    assert bench.profiled_traffic("fp32") == 2.5e8
+    assert bench.profiled_traffic("bf16sr") is None   # no summary for that precision
+
+
+def test_committed_profiles_carry_hash_and_traffic():
+    # every committed sweep summary that states a traffic figure also states
+    # the kernel source it was taken on
+    import glob
+    for f in glob.glob(os.path.join(bench.ROOT, "profiles", "sweep_*_cavity_2048x1024.md")):
+        text = open(f).read()
+        if "dram_bytes_per_launch:" in text:
+            assert "kernel_source_sha256:" in text, f
 
 
 def test_measured_peak_falls_back(tmp_path, monkeypatch):
