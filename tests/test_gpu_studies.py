@@ -36,3 +36,29 @@ def test_srt_departs_when_k1_is_not_1(sweep, k1):
 def test_srt_equals_btrirt_at_k1_1(sweep):
     a, b = sweep[(1.0, "srt")], sweep[(1.0, "btrirt")]
     assert a["max_T_error"] == b["max_T_error"] and a["front_cells"] == b["front_cells"]
+
+
+def test_full_melt_study_resumes_bitwise(tmp_path):
+    """Sec. 3.2's cavities in one batch: a run stopped after every sample and
+    resumed from its FP32 checkpoint ends exactly where an uninterrupted run
+    ends (128 x 128 here, a few thousandths of the Fourier time)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream().cuda_stream
+    kw = dict(n=128, fo_max=0.001, sample_fo=0.00025, stream=s)
+    straight = studies.cavity_full_melt(**kw)
+    calls = 0
+    while True:
+        calls += 1
+        res = studies.cavity_full_melt(checkpoint=str(tmp_path / "ck.npz"), max_seconds=0.0, **kw)
+        if res["complete"]:
+            break
+        assert calls < 10
+    assert calls >= 4
+    assert res["runs"] == straight["runs"]
+    for r in straight["runs"].values():
+        assert r["state"] == "fo_max"
+        h = r["history"]
+        assert h[0][0] == 0.0 and all(row[3] == 0.0 for row in h)
+        assert h[-1][1] > h[0][1]  # melting has started

@@ -1,0 +1,122 @@
+"""Host logic of the full-melting study (Sec. 3.2): threshold crossings, the
+batch membership as cavities finish, and checkpoint / resume -- on CPU, with a
+fake lattice whose melt fraction grows at a fixed rate per step."""
+import numpy as np
+import pytest
+
+from paper_1909_13086_gb300 import studies
+
+
+class FakeLattice:
+    def __init__(self, rate, n=8):
+        self.rate, self.n, self.step_ = rate, n, 0
+        self.f = np.zeros((9, n, n))
+        self.g = np.zeros((9, n, n))
+
+    def derived(self):
+        return {"alpha": 0.01}
+
+    def advance(self, k):
+        self.step_ += k
+        self.f += k          # the "state" remembers every step taken
+        self.g -= 0.5 * k
+
+    def diagnostics(self, raise_on_diverged=True):
+        return {"step": self.step_, "melt_fraction": min(1.0, self.rate * self.step_),
+                "Nu": 2.0, "nan_flag": 0}
+
+    def populations(self):
+        return self.f.copy(), self.g.copy(), self.step_
+
+    def set_populations(self, f, g, step):
+        self.f, self.g, self.step_ = np.array(f, np.float64), np.array(g, np.float64), step
+
+    def close(self):
+        pass
+
+
+class FakeBatch:
+    def __init__(self, k, log):
+        self.members, self.log = [], log
+
+    def add(self, lat):
+        self.members.append(lat)
+
+    def remove(self, lat):
+        self.members.remove(lat)
+
+    def step(self, k):
+        self.log.append(len(self.members))
+        for m in self.members:
+            m.advance(k)
+
+    def close(self):
+        pass
+
+
+RATES = {0.25: 1.0 / 4000, 0.375: 1.0 / 3000, 0.5: 1.0 / 2000}
+
+
+def run(tmp_path=None, max_seconds=None, fo_max=10.0, log=None):
+    log = [] if log is None else log
+    return studies.cavity_full_melt(
+        n=8, centers=tuple(RATES), fo_max=fo_max, sample_fo=0.05, precision="fp32",
+        checkpoint=None if tmp_path is None else str(tmp_path / "ck.npz"), max_seconds=max_seconds,
+        make_lattice=lambda C: FakeLattice(RATES[C]), make_batch=lambda k: FakeBatch(k, log))
+
+
+def test_crossing_interpolates_and_reports_never():
+    h = [(0.1, 0.2, 1.0, 0.0), (0.2, 0.6, 1.0, 0.0), (0.3, 0.95, 1.0, 0.0)]
+    assert studies.crossing_fo(h, 0.5) == pytest.approx(0.175)
+    assert studies.crossing_fo(h, 0.2) == 0.1            # reached at the first sample
+    assert studies.crossing_fo(h, 0.99) is None
+    assert studies.crossing_fo([], 0.5) is None
+
+
+def test_cavities_leave_the_batch_as_they_melt():
+    log = []
+    res = run(log=log)
+    # chunk = 0.05 * 64 / 0.01 = 320 steps; Fo = step / 6400, melt = 6400 rate Fo,
+    # so 0.99 is reached after 7 (C = 0.5), 10 (0.375) and 13 (0.25) samples
+    assert res["steps_per_sample"] == 320
+    assert log == [3] * 7 + [2] * 3 + [1] * 3
+    r = res["runs"]
+    assert [r[str(C)]["state"] for C in RATES] == ["melted"] * 3
+    for C, rate in RATES.items():
+        h = r[str(C)]["history"]
+        assert h[0] == (0.0, 0.0, 2.0, 0.0)           # the initial state comes first
+        for lv in (0.5, 0.9):                          # linear between the samples
+            assert r[str(C)]["fo_at"][str(lv)] == pytest.approx(lv / (6400 * rate))
+    fo99 = [r[str(C)]["fo_at"]["0.99"] for C in RATES]
+    assert fo99[2] < fo99[1] < fo99[0]                 # the centred strip melts first
+
+
+def test_fo_max_stops_unmelted_cavities():
+    res = run(fo_max=0.1)
+    assert {r["state"] for r in res["runs"].values()} == {"fo_max"}
+
+
+def test_resume_from_checkpoint_equals_uninterrupted(tmp_path):
+    straight = run()
+    calls = 0
+    while True:
+        calls += 1
+        res = run(tmp_path, max_seconds=0.0)   # stops after every sample
+        if res["complete"]:
+            break
+        assert calls < 30
+    assert calls == 13  # one sample per call
+    assert res["runs"] == straight["runs"]
+    z = np.load(tmp_path / "ck.npz")
+    assert z["f0"].dtype == np.float32 and int(z["step0"]) == 13 * 320
+    assert np.all(z["f0"] == 13 * 320) and str(z["state2"]) == "melted"
+
+
+def test_checkpoint_of_another_run_and_16_bit_are_rejected(tmp_path):
+    run(tmp_path, max_seconds=0.0)
+    with pytest.raises(ValueError):
+        studies.cavity_full_melt(
+            n=8, centers=(0.25, 0.5), sample_fo=0.5, checkpoint=str(tmp_path / "ck.npz"),
+            make_lattice=lambda C: FakeLattice(RATES[C]), make_batch=lambda k: FakeBatch(k, []))
+    with pytest.raises(ValueError):
+        studies.cavity_full_melt(n=8, precision="bf16sr", checkpoint=str(tmp_path / "x.npz"))
