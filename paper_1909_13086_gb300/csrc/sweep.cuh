@@ -81,6 +81,7 @@ struct Store<float> {
     __device__ static void stg(float *p, float v, uint32_t) { *p = v; }
     __device__ static void stf_rn(float *p, float v) { *p = v; }
     __device__ static void stg_rn(float *p, float v) { *p = v; }
+    __device__ static void st2(float *pg, float *pf, float g, float f, uint32_t) { *pg = g; *pf = f; }
 };
 template <>
 struct Store<double> {
@@ -92,6 +93,10 @@ struct Store<double> {
     __device__ static void stg(double *p, double v, uint32_t) { *p = v; }
     __device__ static void stf_rn(double *p, double v) { *p = v; }
     __device__ static void stg_rn(double *p, double v) { *p = v; }
+    __device__ static void st2(double *pg, double *pf, double g, double f, uint32_t) {
+        *pg = g;
+        *pf = f;
+    }
 };
 
 // Stochastic rounding by "add random bits below the cut, then truncate": a
@@ -103,6 +108,21 @@ struct Store<double> {
 // stays NaN).
 __device__ __forceinline__ float sr_add(float v, uint32_t add) {
     return __uint_as_float(__float_as_uint(v) + add);
+}
+
+// Two floats to 16-bit values in one conversion with stochastic rounding (the
+// sm_100-family cvt with .rs rounding: the 32-bit random operand supplies the
+// bits added below each half's cut).  hi lands in the upper half, lo in the
+// lower half.
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float hi, float lo, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
 }
 
 // FP16 is stored scaled by a power of two (exact): g by 2^6, f - w by 2^10, so
@@ -123,6 +143,12 @@ struct Store<F16<SR>> {
     __device__ static void stg(__half *p, float v, uint32_t r) { enc(p, v * kG, r); }
     __device__ static void stf_rn(__half *p, float v) { *p = __float2half_rn(v * kF); }
     __device__ static void stg_rn(__half *p, float v) { *p = __float2half_rn(v * kG); }
+    // g_i and f_i - w_i of one cell, stochastically rounded together (SR only)
+    __device__ static void st2(__half *pg, __half *pf, float g, float f, uint32_t rbits) {
+        const uint32_t d = cvt_rs_f16x2(g * kG, f * kF, rbits);
+        *pg = __ushort_as_half((unsigned short)(d >> 16));
+        *pf = __ushort_as_half((unsigned short)(d & 0xffffu));
+    }
 };
 // BF16 has FP32's exponent range, so no scaling; 16 bits are discarded.
 template <bool SR>
@@ -140,6 +166,12 @@ struct Store<BF16<SR>> {
     __device__ static void stg(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
     __device__ static void stf_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static void stg_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static void st2(__nv_bfloat16 *pg, __nv_bfloat16 *pf, float g, float f,
+                               uint32_t rbits) {
+        const uint32_t d = cvt_rs_bf16x2(g, f, rbits);
+        *pg = __ushort_as_bfloat16((unsigned short)(d >> 16));
+        *pf = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
+    }
 };
 // Offset added to a stored f value (plane i) to recover f_i.
 template <typename real, typename S>
@@ -149,8 +181,10 @@ __device__ __forceinline__ real f_ofs(int i) {
 
 // Counter-based random bits for stochastic rounding: a 32-bit integer hash
 // (Wellons' "lowbias32" finaliser) of the step seed and the cell index seeds a
-// linear congruential generator (Numerical Recipes' constants), stepped once
-// per stored value; its top 16 bits are used.
+// linear congruential generator (Numerical Recipes' constants).  lcg_next
+// gives the top 16 bits of the next state (one value); lcg_next32 gives 32
+// bits (a pair of values), the state xor its top half shifted down so that the
+// low half does not carry the LCG's short-period low bits.
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352du;
@@ -162,6 +196,10 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 __device__ __forceinline__ uint32_t lcg_next(uint32_t &s) {
     s = s * 1664525u + 1013904223u;
     return s >> 16;
+}
+__device__ __forceinline__ uint32_t lcg_next32(uint32_t &s) {
+    s = s * 1664525u + 1013904223u;
+    return s ^ (s >> 16);
 }
 
 // ---- H -> (T, f_l): H_s = C_p T_m = 0, H_l = H_s + L.
@@ -185,42 +223,46 @@ __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // p_i <- a p_i + w_i [B0 + 3 c_i.B1 + 9/2 Q_i:B2]  for all nine directions.
+// With X = B2xx, Y = B2yy, Z = B2xy, S = X + Y and Q_i = c_i c_i - I/3, the
+// products w_i * 9/2 Q_i:B2 are -2S/3 (rest), X/3 - Y/6 (+-x), Y/3 - X/6
+// (+-y), S/12 + Z/4 (diagonals 5, 7) and S/12 - Z/4 (6, 8); w_i * 3 c_i.B1 is
+// +-B1x/3, +-B1y/3, +-(B1x + B1y)/12 and +-(B1y - B1x)/12.
 template <typename real>
 __device__ __forceinline__ void emit(real p[9], real a, real B0, real B1x, real B1y, real B2xx,
                                      real B2xy, real B2yy) {
-    const real third = real(1) / real(3);
+    const real third = real(1) / real(3), sixth = real(1) / real(6), twelfth = real(1) / real(12);
     const real w0 = real(4) / real(9), w1 = real(1) / real(9), w5 = real(1) / real(36);
-    const real q0 = -(B2xx + B2yy) * third;
-    const real q13 = (real(2) * B2xx - B2yy) * third;
-    const real q24 = (real(2) * B2yy - B2xx) * third;
-    const real s = real(2) * third * (B2xx + B2yy);
-    const real q57 = s + real(2) * B2xy;
-    const real q68 = s - real(2) * B2xy;
-    p[0] = a * p[0] + w0 * (B0 + real(4.5) * q0);
-    const real e13 = w1 * (B0 + real(4.5) * q13), t1 = real(3) * w1 * B1x;
+    const real S = B2xx + B2yy;
+    p[0] = a * p[0] + (w0 * B0 - (real(2) / real(3)) * S);
+    const real W1 = w1 * B0;
+    const real e13 = W1 + third * B2xx - sixth * B2yy, t1 = third * B1x;
     p[1] = a * p[1] + (e13 + t1);
     p[3] = a * p[3] + (e13 - t1);
-    const real e24 = w1 * (B0 + real(4.5) * q24), t2 = real(3) * w1 * B1y;
+    const real e24 = W1 + third * B2yy - sixth * B2xx, t2 = third * B1y;
     p[2] = a * p[2] + (e24 + t2);
     p[4] = a * p[4] + (e24 - t2);
-    const real e57 = w5 * (B0 + real(4.5) * q57), t5 = real(3) * w5 * (B1x + B1y);
+    const real e5 = w5 * B0 + twelfth * S, z4 = real(0.25) * B2xy;
+    const real e57 = e5 + z4, t5 = twelfth * (B1x + B1y);
     p[5] = a * p[5] + (e57 + t5);
     p[7] = a * p[7] + (e57 - t5);
-    const real e68 = w5 * (B0 + real(4.5) * q68), t6 = real(3) * w5 * (B1y - B1x);
+    const real e68 = e5 - z4, t6 = twelfth * (B1y - B1x);
     p[6] = a * p[6] + (e68 + t6);
     p[8] = a * p[8] + (e68 - t6);
 }
 
-// Raw first and second moments of nine populations.
+// Raw first and second moments of nine populations (the diagonal pairs'
+// sums and differences shared).
 template <typename real>
 __device__ __forceinline__ void raw_moments(const real p[9], real &jx, real &jy, real &pxx,
                                             real &pxy, real &pyy) {
-    jx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
-    jy = (p[2] - p[4]) + (p[5] + p[6]) - (p[7] + p[8]);
-    const real d = (p[5] + p[6]) + (p[7] + p[8]);
+    const real s57 = p[5] + p[7], s68 = p[6] + p[8];
+    const real d57 = p[5] - p[7], d68 = p[6] - p[8];
+    jx = (p[1] - p[3]) + (d57 - d68);
+    jy = (p[2] - p[4]) + (d57 + d68);
+    const real d = s57 + s68;
     pxx = (p[1] + p[3]) + d;
     pyy = (p[2] + p[4]) + d;
-    pxy = (p[5] + p[7]) - (p[6] + p[8]);
+    pxy = s57 - s68;
 }
 
 template <typename real>
@@ -238,12 +280,11 @@ struct Macro {
 template <typename real, bool FLOW, bool COLLIDE>
 __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, real f[9], real g[9]) {
     Macro<real> m;
-    real jx = real(0), jy = real(0);
+    real fjx = real(0), fjy = real(0), fxx = real(0), fxy = real(0), fyy = real(0);
     m.rho = real(1);
     if (FLOW) {
         m.rho = sum9(f);
-        jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        raw_moments(f, fjx, fjy, fxx, fxy, fyy);
     }
     m.H = sum9(g);
     invert(m.H, a.Lh, a.inv_Lh, m.T, m.fl);
@@ -253,8 +294,8 @@ __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, rea
     if (FLOW) {
         Fy = a.gbeta * m.T;
         const real inv_rho = recip(m.rho);
-        m.ux = m.fl * jx * inv_rho;
-        m.uy = m.fl * (jy + real(0.5) * Fy) * inv_rho;
+        m.ux = m.fl * fjx * inv_rho;
+        m.uy = m.fl * (fjy + real(0.5) * Fy) * inv_rho;
     }
     if (!COLLIDE) return m;
 
@@ -274,8 +315,6 @@ __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, rea
     }
     // ---- f (same block operator, forcing folded into A1 and A2)
     if (FLOW) {
-        real fjx, fjy, fxx, fxy, fyy;
-        raw_moments(f, fjx, fjy, fxx, fxy, fyy);
         const real rho = m.rho, ux = m.ux, uy = m.uy;
         const real rux = rho * ux, ruy = rho * uy;
         const real rxx = rux * ux, rxy = rux * uy, ryy = ruy * uy, r3 = rho * third;
@@ -600,8 +639,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
             uint32_t rs = hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x));
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                Store<S>::stg(d + (9 + i) * kTW, g[i], lcg_next(rs));
-                if (FLOW) Store<S>::stf(d + i * kTW, f[i] - f_ofs<real, S>(i), lcg_next(rs));
+                if (FLOW)
+                    Store<S>::st2(d + (9 + i) * kTW, d + i * kTW, g[i], f[i] - f_ofs<real, S>(i),
+                                  lcg_next32(rs));
+                else
+                    Store<S>::stg(d + (9 + i) * kTW, g[i], lcg_next(rs));
             }
         }
         if (MODE == kSweepDiag) {
