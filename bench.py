@@ -40,8 +40,8 @@ METRIC = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
 # FP64 operations (adds, subtracts, multiplies, one divide; an FMA counts as
 # two) in one interior-cell update as the sweep writes it out: macroscopic
-# fields 35, g collision 104, f collision 126.
-FP64_FLOPS_PER_LUP = 265
+# fields with the raw moments of f 41, g collision 90, f collision 96.
+FP64_FLOPS_PER_LUP = 227
 # GB300 FP64 pipe: 2 FMA per clock per SM, 2 flops each, 152 SMs, 2070 MHz.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_13086_gb300", "csrc", f)

@@ -147,10 +147,11 @@ int lbm_set_diag_every(lbm_handle h, long long k);
 /* Launch shape of the sweep (the tuner's knobs): rows of the lattice walked by
  * each thread of a block (1 to 1024, default 1); the distance, in rows, at
  * which each block asks L2 to prefetch a later block's tile row (0 = off,
- * default 4); and graph_chunk, the number of sweeps lbm_step captures once into
- * a CUDA graph and then replays (0 = launch every sweep directly; default 128;
- * up to 8 chunk graphs are cached per handle, keyed by buffer parity and the
- * position of the diagnostic sweeps).  When the caller is itself capturing the
+ * default 4, or 24 with 16-bit storage); and graph_chunk, the number of
+ * sweeps lbm_step captures once into a CUDA graph and then replays (0 =
+ * launch every sweep directly; default 128; up to 8 chunk graphs are cached
+ * per handle, keyed by buffer parity and the position of the diagnostic
+ * sweeps).  When the caller is itself capturing the
  * handle's stream, lbm_step launches directly.  Results do not depend on any
  * of these, except the rounding of the in-warp partial sums of the FP32
  * diagnostics.  Errors: LBM_ERR_ARG. */

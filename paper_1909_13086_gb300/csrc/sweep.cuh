@@ -178,6 +178,18 @@ template <typename real, typename S>
 __device__ __forceinline__ real f_ofs(int i) {
     return Store<S>::kDev ? w_of<real>(i) : real(0);
 }
+// f_i and g_i from their stored values.  The offset is added only where the
+// codec has one: x + 0 is not an identity in IEEE arithmetic (-0 + 0 = +0), so
+// adding a zero offset would cost an instruction per population.
+template <typename real, typename S>
+__device__ __forceinline__ real ld_f(const typename Store<S>::elem *p, int i) {
+    if constexpr (Store<S>::kDev) return Store<S>::ldf(p) + w_of<real>(i);
+    else return Store<S>::ldf(p);
+}
+template <typename real, typename S>
+__device__ __forceinline__ real ld_g(const typename Store<S>::elem *p, int) {
+    return Store<S>::ldg(p);
+}
 
 // Counter-based random bits for stochastic rounding: a 32-bit integer hash
 // (Wellons' "lowbias32" finaliser) of the step seed and the cell index seeds a
@@ -342,26 +354,21 @@ __device__ __forceinline__ void pull_fast(const typename Store<S>::elem *__restr
                                           const typename Store<S>::elem *__restrict__ bR, real f[9],
                                           real g[9]) {
     constexpr int R = kRS, W = kTW;
-    using St = Store<S>;
-#define BTRIRT_PULL(P, arr, LD, OFS)                                     \
-    arr[0] = St::LD(b + (P + 0) * W) + OFS(0);                           \
-    arr[1] = St::LD(bL + (P + 1) * W - 1) + OFS(1);                      \
-    arr[2] = St::LD(b + (P + 2) * W - R) + OFS(2);                       \
-    arr[3] = St::LD(bR + (P + 3) * W + 1) + OFS(3);                      \
-    arr[4] = St::LD(b + (P + 4) * W + R) + OFS(4);                       \
-    arr[5] = St::LD(bL + (P + 5) * W - R - 1) + OFS(5);                  \
-    arr[6] = St::LD(bR + (P + 6) * W - R + 1) + OFS(6);                  \
-    arr[7] = St::LD(bR + (P + 7) * W + R + 1) + OFS(7);                  \
-    arr[8] = St::LD(bL + (P + 8) * W + R - 1) + OFS(8);
-#define BTRIRT_NOOFS(i) real(0)
-#define BTRIRT_FOFS(i) f_ofs<real, S>(i)
-    BTRIRT_PULL(9, g, ldg, BTRIRT_NOOFS)
+#define BTRIRT_PULL(P, arr, LD)                             \
+    arr[0] = LD<real, S>(b + (P + 0) * W, 0);               \
+    arr[1] = LD<real, S>(bL + (P + 1) * W - 1, 1);          \
+    arr[2] = LD<real, S>(b + (P + 2) * W - R, 2);           \
+    arr[3] = LD<real, S>(bR + (P + 3) * W + 1, 3);          \
+    arr[4] = LD<real, S>(b + (P + 4) * W + R, 4);           \
+    arr[5] = LD<real, S>(bL + (P + 5) * W - R - 1, 5);      \
+    arr[6] = LD<real, S>(bR + (P + 6) * W - R + 1, 6);      \
+    arr[7] = LD<real, S>(bR + (P + 7) * W + R + 1, 7);      \
+    arr[8] = LD<real, S>(bL + (P + 8) * W + R - 1, 8);
+    BTRIRT_PULL(9, g, ld_g)
     if (FLOW) {
-        BTRIRT_PULL(0, f, ldf, BTRIRT_FOFS)
+        BTRIRT_PULL(0, f, ld_f)
     }
 #undef BTRIRT_PULL
-#undef BTRIRT_NOOFS
-#undef BTRIRT_FOFS
 }
 
 // Any cell: explicit source test per direction and the wall rules.
@@ -379,7 +386,7 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
         const long long cell = in ? pop_index(sx, sy, 0, a.ny) : self;
         const int pl = in ? i : opp_of(i);
         real gv = Store<S>::ldg(src + cell + (9 + pl) * kTW);
-        if (FLOW) f[i] = Store<S>::ldf(src + cell + pl * kTW) + f_ofs<real, S>(pl);
+        if (FLOW) f[i] = ld_f<real, S>(src + cell + pl * kTW, pl);
         if (!in) {
             bool heated;
             if (PROB == kStefan) {
