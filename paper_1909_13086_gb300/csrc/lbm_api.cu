@@ -822,7 +822,9 @@ struct lbm_batch_s {
     std::vector<lbm_s *> members;
     void *entries = nullptr;  // device table: max BatchEntry<real>
     int *parity = nullptr;    // device: source buffer of each member
+    int *starts = nullptr;    // device: first block of each member
     std::vector<unsigned char> host_entries;
+    std::vector<int> host_starts;
     std::vector<int> host_parity;
     int nblocks = 0;
     bool dirty = true;        // table must be rebuilt and uploaded
@@ -868,6 +870,7 @@ template <typename real>
 void batch_build(lbm_batch_s *b) {
     const size_t eb = entry_bytes<real>();
     b->host_entries.assign(eb * b->members.size(), 0);
+    b->host_starts.assign(b->members.size(), 0);
     int start = 0;
     for (size_t r = 0; r < b->members.size(); ++r) {
         lbm_s *h = b->members[r];
@@ -877,6 +880,7 @@ void batch_build(lbm_batch_s *b) {
             e.a[p].parity = p;
         }
         e.start = start;
+        b->host_starts[r] = start;
         e.gx = (int)h->grid.x;
         e.gy = (int)h->grid.y;
         start += e.gx * e.gy;
@@ -891,6 +895,8 @@ int batch_steps(lbm_batch_s *b, long long n) {
     if (b->dirty) {
         batch_build<real>(b);
         BATCH_TRY(cudaMemcpyAsync(b->entries, b->host_entries.data(), b->host_entries.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+        BATCH_TRY(cudaMemcpyAsync(b->starts, b->host_starts.data(), b->host_starts.size() * sizeof(int),
                                   cudaMemcpyHostToDevice, b->stream));
         batch_drop_graph(b);
         b->dirty = false;
@@ -909,8 +915,8 @@ int batch_steps(lbm_batch_s *b, long long n) {
             BATCH_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
             for (int j = 0; j < K && e == cudaSuccess; ++j)
-                e = launch_batch<real, S>(b->entries, b->parity, nm, b->nblocks, b->problem, b->flow != 0,
-                                          false, j, b->stream);
+                e = launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->nblocks, b->problem,
+                                          b->flow != 0, false, j, b->stream);
             cudaGraph_t g = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
             if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -929,8 +935,9 @@ int batch_steps(lbm_batch_s *b, long long n) {
         done += K;
     }
     for (; done < n; ++done) {
-        const cudaError_t e = launch_batch<real, S>(b->entries, b->parity, nm, b->nblocks, b->problem,
-                                                    b->flow != 0, done == n - 1, (int)(done & 1), b->stream);
+        const cudaError_t e =
+            launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->nblocks, b->problem, b->flow != 0,
+                                  done == n - 1, (int)(done & 1), b->stream);
         if (e != cudaSuccess) return batch_err(LBM_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
     }
     for (lbm_s *h : b->members) {
@@ -968,7 +975,7 @@ int lbm_batch_create(int max_lattices, void *cuda_stream, lbm_batch *out) {
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
     const size_t table = ((size_t)max_lattices * sizeof(BatchEntry<double>) + 255) / 256 * 256;
-    const size_t bytes = table + (size_t)max_lattices * sizeof(int);
+    const size_t bytes = table + 2 * (size_t)max_lattices * sizeof(int);
     void *mem = nullptr;
     if (e == cudaSuccess) {
         if (b->alloc) {
@@ -984,6 +991,7 @@ int lbm_batch_create(int max_lattices, void *cuda_stream, lbm_batch *out) {
     }
     b->entries = mem;
     b->parity = reinterpret_cast<int *>(static_cast<char *>(mem) + table);
+    b->starts = b->parity + max_lattices;
     *out = b;
     return LBM_OK;
 }

@@ -371,6 +371,34 @@ __device__ __forceinline__ void pull_fast(const typename Store<S>::elem *__restr
 #undef BTRIRT_PULL
 }
 
+// Half-way bounce-back at the cavity's adiabatic no-slip side walls for a cell
+// of an interior row, after pull_fast: the directions whose source lies beyond
+// x = 0 (c_x = +1: 1, 5, 8) or beyond x = nx - 1 (c_x = -1: 3, 6, 7) take the
+// cell's own post-collision opposite populations, as pull_any does.
+template <typename real, typename S, bool FLOW>
+__device__ __forceinline__ void bounce_side_walls(const typename Store<S>::elem *b, int x, int nx,
+                                                  real f[9], real g[9]) {
+    constexpr int W = kTW;
+    if (x == 0) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (cx_of(i) != 1) continue;
+            const int o = opp_of(i);
+            g[i] = ld_g<real, S>(b + (9 + o) * W, o);
+            if (FLOW) f[i] = ld_f<real, S>(b + o * W, o);
+        }
+    }
+    if (x == nx - 1) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (cx_of(i) != -1) continue;
+            const int o = opp_of(i);
+            g[i] = ld_g<real, S>(b + (9 + o) * W, o);
+            if (FLOW) f[i] = ld_f<real, S>(b + o * W, o);
+        }
+    }
+}
+
 // Any cell: explicit source test per direction and the wall rules.
 template <typename real, typename S, int PROB, bool FLOW>
 __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y, real f[9],
@@ -604,12 +632,17 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
     // the warp's 32 columns are clear of both side walls (warp-uniform)
     const int xw = bx * kTW + (lx & ~31);
     const bool fastcol = xw >= 1 && xw + 31 <= a.nx - 2;
+    // A cavity warp that touches a side wall also takes the fast loads on the
+    // interior rows: the wall lane's out-of-lattice neighbour pointer is
+    // clamped to its own cell (the loads then stay inside its tile row) and
+    // its wall directions are replaced by bounce-back afterwards.
+    const bool sidewall = PROB == kCavity && !fastcol;
 
     long long i0 = 0, iL = 0, iR = 0;
-    if (fastcol) {
+    if (fastcol || sidewall) {
         i0 = pop_index(x, y0, 0, a.ny);
-        iL = (lx == 0) ? pop_index(x - 1, y0, 0, a.ny) + 1 : i0;
-        iR = (lx == kTW - 1) ? pop_index(x + 1, y0, 0, a.ny) - 1 : i0;
+        iL = (lx == 0 && x > 0) ? pop_index(x - 1, y0, 0, a.ny) + 1 : i0;
+        iR = (lx == kTW - 1 && x < a.nx - 1) ? pop_index(x + 1, y0, 0, a.ny) - 1 : i0;
     }
 
     real q = real(0);
@@ -618,8 +651,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
     for (int y = y0; y < y1; ++y, i0 += kRS, iL += kRS, iR += kRS) {
         if (!active) continue;
         real f[9], g[9];
-        if (fastcol && y >= 1 && y <= a.ny - 2) {
+        if ((fastcol || sidewall) && y >= 1 && y <= a.ny - 2) {
             pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
+            if (sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
         } else {
             pull_any<real, S, PROB, FLOW>(a, x, y, f, g, q);
         }
@@ -714,43 +748,43 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
 }
 
 // ---- batches: many lattices of one precision and problem kind per launch ----
-// Block b of a batch launch belongs to the entry r with start[r] <= b <
-// start[r + 1]; within it, local block l = b - start[r] is tile column l % gx,
-// row band l / gx.  Each entry holds the lattice's arguments for both buffer
-// parities; the launch for step j of a chunk uses parity parity[r] ^ (j & 1).
-// The entry's arguments are staged in shared memory once per block.
-template <typename real>
-__device__ __forceinline__ int batch_find(const BatchEntry<real> *e, int n, int b) {
-    int lo = 0, hi = n - 1;  // last entry with start <= b
+// Block b of a batch launch belongs to the entry r with starts[r] <= b <
+// starts[r + 1]; within it, local block l = b - starts[r] is tile column
+// l % gx, row band l / gx.  Each entry holds the lattice's arguments for both
+// buffer parities; the launch for step j of a chunk uses parity
+// parity[r] ^ (j & 1).  The block's start-up is two dependent reads: the
+// search over the compact starts array (its first lines stay in L1 for the
+// blocks an SM runs), then the whole entry, copied into shared memory 16 bytes
+// per thread, alongside the parity word.
+__device__ __forceinline__ int batch_find(const int *starts, int n, int b) {
+    int lo = 0, hi = n - 1;  // last entry with starts[r] <= b
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&e[mid].start) <= b) lo = mid; else hi = mid - 1;
+        if (__ldg(starts + mid) <= b) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
 template <typename real, typename S, int PROB, bool FLOW, int MODE>
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
-    batch_kernel(const BatchEntry<real> *entries, const int *parity, int n, int j) {
+    batch_kernel(const BatchEntry<real> *entries, const int *starts, const int *parity, int n,
+                 int j) {
+    static_assert(sizeof(BatchEntry<real>) % 16 == 0, "entries are copied in 16-byte pieces");
     __shared__ double sh[32 * 4];
-    __shared__ __align__(16) unsigned char args_sh[sizeof(SweepArgs<real>)];
-    __shared__ int meta[3];
-    if (threadIdx.x == 0) {
-        const int r = batch_find(entries, n, blockIdx.x);
-        const int p = __ldg(parity + r) ^ (j & 1);
-        const int l = blockIdx.x - __ldg(&entries[r].start);
-        const int gx = __ldg(&entries[r].gx);
-        meta[0] = l % gx;
-        meta[1] = l / gx;
-        meta[2] = gx;
-        // stage the arguments of (r, p)
-        const int4 *s4 = reinterpret_cast<const int4 *>(&entries[r].a[p]);
-        int4 *d4 = reinterpret_cast<int4 *>(args_sh);
-        for (unsigned k = 0; k < sizeof(SweepArgs<real>) / 16; ++k) d4[k] = __ldg(s4 + k);
-    }
+    __shared__ __align__(16) unsigned char entry_sh[sizeof(BatchEntry<real>)];
+    __shared__ int meta[2];
+    if (threadIdx.x == 0) meta[0] = batch_find(starts, n, blockIdx.x);
     __syncthreads();
-    const SweepArgs<real> &a = *reinterpret_cast<const SweepArgs<real> *>(args_sh);
-    sweep_block<real, S, PROB, FLOW, MODE>(a, meta[0], meta[1], meta[2], sh);
+    const int r = meta[0];
+    const int4 *s4 = reinterpret_cast<const int4 *>(entries + r);
+    int4 *d4 = reinterpret_cast<int4 *>(entry_sh);
+    for (unsigned k = threadIdx.x; k < sizeof(BatchEntry<real>) / 16; k += blockDim.x)
+        d4[k] = __ldg(s4 + k);
+    if (threadIdx.x == 0) meta[1] = __ldg(parity + r) ^ (j & 1);
+    __syncthreads();
+    const BatchEntry<real> &e = *reinterpret_cast<const BatchEntry<real> *>(entry_sh);
+    const int l = blockIdx.x - e.start;
+    sweep_block<real, S, PROB, FLOW, MODE>(e.a[meta[1]], l % e.gx, l / e.gx, e.gx, sh);
 }
 
 // Per-entry diagnostics fold after a diagnostic batch step: block r folds the
@@ -941,15 +975,16 @@ cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int
 }
 
 template <typename real, typename S>
-cudaError_t launch_batch(const void *entries, const int *parity, int n, int nblocks, int problem,
-                         bool flow, bool diag, int j, cudaStream_t s) {
+cudaError_t launch_batch(const void *entries, const int *starts, const int *parity, int n,
+                         int nblocks, int problem, bool flow, bool diag, int j, cudaStream_t s) {
     const BatchEntry<real> *e = static_cast<const BatchEntry<real> *>(entries);
     const dim3 grid(nblocks), block(kTW);
-#define BTRIRT_BATCH(PROB, FLOW)                                                                 \
-    if (diag)                                                                                    \
-        batch_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(e, parity, n, j);   \
-    else                                                                                         \
-        batch_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(e, parity, n, j);
+#define BTRIRT_BATCH(PROB, FLOW)                                                                   \
+    if (diag)                                                                                      \
+        batch_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(e, starts, parity, n, \
+                                                                             j);                   \
+    else                                                                                           \
+        batch_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(e, starts, parity, n, j);
     if (problem == kCavity) {
         if (flow) { BTRIRT_BATCH(kCavity, true) } else { BTRIRT_BATCH(kCavity, false) }
     } else {
@@ -1000,7 +1035,7 @@ cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, 
     template cudaError_t launch_fields0<REAL, S>(const SweepArgs<REAL> &, bool, dim3, dim3,      \
                                                  cudaStream_t);                                  \
     template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t); \
-    template cudaError_t launch_batch<REAL, S>(const void *, const int *, int, int, int, bool, bool, \
-                                               int, cudaStream_t);
+    template cudaError_t launch_batch<REAL, S>(const void *, const int *, const int *, int, int,  \
+                                               int, bool, bool, int, cudaStream_t);
 
 }  // namespace btrirt
