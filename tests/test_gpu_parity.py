@@ -132,6 +132,29 @@ def test_single_step_from_random_state(orc, stream, prec, tol, problem):
                                                          abs=10 * tol)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("nx", [2, 31, 33, 128, 129, 256])
+def test_side_wall_columns_from_random_state(orc, stream, prec, tol, nx):
+    """Side-wall warps of the cavity take the fast loads and bounce their wall
+    lane back: checked where a warp touches both walls (2, 31), where the last
+    column is a lone lane of a later warp (33, 129) and where it ends a tile
+    (128, 256), one step from arbitrary populations."""
+    ny, p = 9, workloads.params(Ra=1e6, strip_center=0.5, strip_width=0.5)
+    f, g = workloads.random_populations(nx, ny, seed=nx)
+    if prec == "fp32":
+        f, g = f.astype(np.float32).astype(np.float64), g.astype(np.float32).astype(np.float64)
+    ref = orc.Oracle(nx, ny, **p)
+    ref.set_populations(f, g, step=3)
+    ref.step(1)
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    lat.set_populations(f, g, step=3)
+    lat.step(1)
+    fo, go, _ = lat.populations()
+    fr, gr = ref.populations()
+    assert np.abs(go - gr).max() <= tol * max(1.0, np.abs(gr).max())
+    assert np.abs(fo - fr).max() <= tol * max(1.0, np.abs(fr).max())
+
+
 # ------------------------------------------------------------ FP32 parity
 def test_fp32_cavity_1000_steps(orc, stream):
     nx, ny, p = workloads.cavity_64x32()
