@@ -82,6 +82,12 @@ struct Store<float> {
     __device__ static void stf_rn(float *p, float v) { *p = v; }
     __device__ static void stg_rn(float *p, float v) { *p = v; }
     __device__ static void st2(float *pg, float *pf, float g, float f, uint32_t) { *pg = g; *pf = f; }
+    // stored units (see the 16-bit codecs): the values themselves
+    static constexpr float kF = 1.0f, kG = 1.0f;
+    __device__ static float ldr(const float *p) { return __ldg(p); }
+    __device__ static void str_rn(float *p, float v) { *p = v; }
+    __device__ static void strs(float *p, float v, uint32_t) { *p = v; }
+    __device__ static void st2r(float *pg, float *pf, float g, float f, uint32_t) { *pg = g; *pf = f; }
 };
 template <>
 struct Store<double> {
@@ -94,6 +100,14 @@ struct Store<double> {
     __device__ static void stf_rn(double *p, double v) { *p = v; }
     __device__ static void stg_rn(double *p, double v) { *p = v; }
     __device__ static void st2(double *pg, double *pf, double g, double f, uint32_t) {
+        *pg = g;
+        *pf = f;
+    }
+    static constexpr double kF = 1.0, kG = 1.0;
+    __device__ static double ldr(const double *p) { return __ldg(p); }
+    __device__ static void str_rn(double *p, double v) { *p = v; }
+    __device__ static void strs(double *p, double v, uint32_t) { *p = v; }
+    __device__ static void st2r(double *pg, double *pf, double g, double f, uint32_t) {
         *pg = g;
         *pf = f;
     }
@@ -145,7 +159,14 @@ struct Store<F16<SR>> {
     __device__ static void stg_rn(__half *p, float v) { *p = __float2half_rn(v * kG); }
     // g_i and f_i - w_i of one cell, stochastically rounded together (SR only)
     __device__ static void st2(__half *pg, __half *pf, float g, float f, uint32_t rbits) {
-        const uint32_t d = cvt_rs_f16x2(g * kG, f * kF, rbits);
+        st2r(pg, pf, g * kG, f * kF, rbits);
+    }
+    // stored units: g_i kG and (f_i - w_i) kF, converted without scaling
+    __device__ static float ldr(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static void str_rn(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static void strs(__half *p, float v, uint32_t r) { enc(p, v, r); }
+    __device__ static void st2r(__half *pg, __half *pf, float g, float f, uint32_t rbits) {
+        const uint32_t d = cvt_rs_f16x2(g, f, rbits);
         *pg = __ushort_as_half((unsigned short)(d >> 16));
         *pf = __ushort_as_half((unsigned short)(d & 0xffffu));
     }
@@ -168,6 +189,15 @@ struct Store<BF16<SR>> {
     __device__ static void stg_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static void st2(__nv_bfloat16 *pg, __nv_bfloat16 *pf, float g, float f,
                                uint32_t rbits) {
+        st2r(pg, pf, g, f, rbits);
+    }
+    // stored units: g_i and f_i - w_i (no scaling)
+    static constexpr float kF = 1.0f, kG = 1.0f;
+    __device__ static float ldr(const __nv_bfloat16 *p) { return ld(p); }
+    __device__ static void str_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static void strs(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
+    __device__ static void st2r(__nv_bfloat16 *pg, __nv_bfloat16 *pf, float g, float f,
+                                uint32_t rbits) {
         const uint32_t d = cvt_rs_bf16x2(g, f, rbits);
         *pg = __ushort_as_bfloat16((unsigned short)(d >> 16));
         *pf = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
@@ -178,17 +208,17 @@ template <typename real, typename S>
 __device__ __forceinline__ real f_ofs(int i) {
     return Store<S>::kDev ? w_of<real>(i) : real(0);
 }
-// f_i and g_i from their stored values.  The offset is added only where the
-// codec has one: x + 0 is not an identity in IEEE arithmetic (-0 + 0 = +0), so
-// adding a zero offset would cost an instruction per population.
+// The sweep works in stored units: f as stored (f_i itself, or the scaled
+// deviation (f_i - w_i) kF of the 16-bit codecs) and g_i kG, so that no
+// population is rescaled or offset on its way in or out; cell_update carries
+// the scales and the rest state in a few per-cell terms instead.
 template <typename real, typename S>
-__device__ __forceinline__ real ld_f(const typename Store<S>::elem *p, int i) {
-    if constexpr (Store<S>::kDev) return Store<S>::ldf(p) + w_of<real>(i);
-    else return Store<S>::ldf(p);
+__device__ __forceinline__ real ld_f(const typename Store<S>::elem *p, int) {
+    return Store<S>::ldr(p);
 }
 template <typename real, typename S>
 __device__ __forceinline__ real ld_g(const typename Store<S>::elem *p, int) {
-    return Store<S>::ldg(p);
+    return Store<S>::ldr(p);
 }
 
 // Counter-based random bits for stochastic rounding: a 32-bit integer hash
@@ -288,26 +318,43 @@ struct Macro {
 };
 
 // Steps 2-5 on one cell: macroscopic fields, then both collisions in place
-// (COLLIDE = false stops after the fields).
-template <typename real, bool FLOW, bool COLLIDE>
+// (COLLIDE = false stops after the fields).  f and g are in stored units (see
+// ld_f); the returned fields are physical.  With the 16-bit codecs f holds
+// delta_i = (f_i - w_i) kF: its raw moments are kF times those of f less the
+// rest state's (j; the second moments less I/3), rho = 1 + sum(delta) / kF,
+// and the block collision of delta is that of f with B0 = k0 (rho - 1) kF,
+// since a + k0 = 1 cancels the rest state; g holds g_i kG and collides with
+// T kG and H kG in place of T and H.
+template <typename real, typename S, bool FLOW, bool COLLIDE>
 __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, real f[9], real g[9]) {
+    constexpr bool kDev = Store<S>::kDev;
+    constexpr real kF = real(Store<S>::kF), kG = real(Store<S>::kG);
     Macro<real> m;
-    real fjx = real(0), fjy = real(0), fxx = real(0), fxy = real(0), fyy = real(0);
+    real fs = real(0), fjx = real(0), fjy = real(0), fxx = real(0), fxy = real(0), fyy = real(0);
     m.rho = real(1);
     if (FLOW) {
-        m.rho = sum9(f);
+        fs = sum9(f);
         raw_moments(f, fjx, fjy, fxx, fxy, fyy);
+        if constexpr (kDev) m.rho = real(1) + fs * (real(1) / kF);
+        else m.rho = fs;
     }
-    m.H = sum9(g);
+    const real Hs = sum9(g);
+    if constexpr (kG != real(1)) m.H = Hs * (real(1) / kG);
+    else m.H = Hs;
     invert(m.H, a.Lh, a.inv_Lh, m.T, m.fl);
-    real Fy = real(0);
+    real Fy = real(0), Fk = real(0);
     m.ux = real(0);
     m.uy = real(0);
     if (FLOW) {
         Fy = a.gbeta * m.T;
-        const real inv_rho = recip(m.rho);
-        m.ux = m.fl * fjx * inv_rho;
-        m.uy = m.fl * (fjy + real(0.5) * Fy) * inv_rho;
+        real iu = recip(m.rho);
+        Fk = Fy;
+        if constexpr (kF != real(1)) {
+            iu = iu * (real(1) / kF);
+            Fk = Fy * kF;
+        }
+        m.ux = m.fl * fjx * iu;
+        m.uy = m.fl * (fjy + real(0.5) * Fk) * iu;
     }
     if (!COLLIDE) return m;
 
@@ -316,29 +363,35 @@ __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, rea
     {
         real gjx, gjy, gxx, gxy, gyy;
         raw_moments(g, gjx, gjy, gxx, gxy, gyy);
-        const real T = m.T, T3 = m.T * third;
+        real T = m.T;
+        if constexpr (kG != real(1)) T = m.T * kG;
+        const real T3 = T * third;
         const real d1 = a.k1 - a.k0, d2 = a.k2 - a.k0;
         const real k0T = a.k0 * T;
         const real B1x = k0T * m.ux - d1 * (gjx - T * m.ux);
         const real B1y = k0T * m.uy - d1 * (gjy - T * m.uy);
-        const real H = m.H;
         emit(g, real(1) - a.k0, k0T, B1x, B1y, -d2 * (gxx - T3), -d2 * gxy, -d2 * (gyy - T3));
-        g[0] += a.k0 * (H - T);
+        g[0] += a.k0 * (Hs - T);
     }
     // ---- f (same block operator, forcing folded into A1 and A2)
     if (FLOW) {
-        const real rho = m.rho, ux = m.ux, uy = m.uy;
-        const real rux = rho * ux, ruy = rho * uy;
-        const real rxx = rux * ux, rxy = rux * uy, ryy = ruy * uy, r3 = rho * third;
+        const real ux = m.ux, uy = m.uy;
+        real rk = m.rho, R0 = m.rho;  // rho in stored units; the density term of B0
+        if constexpr (kDev) {
+            R0 = fs;
+            if constexpr (kF != real(1)) rk = m.rho * kF;
+        }
+        const real rux = rk * ux, ruy = rk * uy;
+        const real rxx = rux * ux, rxy = rux * uy, ryy = ruy * uy, r3 = R0 * third;
         const real d1 = a.k1f - a.k0f, d2 = a.k2f - a.k0f;
         const real s1 = real(1) - real(0.5) * a.k1f, s2 = real(1) - real(0.5) * a.k2f;
         const real A1x = d1 * (fjx - rux);
-        const real A1y = d1 * (fjy - ruy) - s1 * Fy;
+        const real A1y = d1 * (fjy - ruy) - s1 * Fk;
         const real A2xx = d2 * (fxx - r3 - rxx);
-        const real A2xy = d2 * (fxy - rxy) - s2 * ux * Fy;
-        const real A2yy = d2 * (fyy - r3 - ryy) - s2 * real(2) * uy * Fy;
+        const real A2xy = d2 * (fxy - rxy) - s2 * ux * Fk;
+        const real A2yy = d2 * (fyy - r3 - ryy) - s2 * real(2) * uy * Fk;
         const real k0 = a.k0f;
-        emit(f, real(1) - k0, k0 * rho, k0 * rux - A1x, k0 * ruy - A1y, k0 * rxx - A2xx,
+        emit(f, real(1) - k0, k0 * R0, k0 * rux - A1x, k0 * ruy - A1y, k0 * rxx - A2xx,
              k0 * rxy - A2xy, k0 * ryy - A2yy);
     }
     return m;
@@ -413,7 +466,7 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
         const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
         const long long cell = in ? pop_index(sx, sy, 0, a.ny) : self;
         const int pl = in ? i : opp_of(i);
-        real gv = Store<S>::ldg(src + cell + (9 + pl) * kTW);
+        real gv = ld_g<real, S>(src + cell + (9 + pl) * kTW, pl);
         if (FLOW) f[i] = ld_f<real, S>(src + cell + pl * kTW, pl);
         if (!in) {
             bool heated;
@@ -424,8 +477,9 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
                 heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
             }
             if (heated) {
-                const real wt = real(2) * w_of<real>(i);  // 2 w_i C_p T_h, T_h = 1
-                q += wt - real(2) * gv;
+                // 2 w_i C_p T_h (T_h = 1), in g's stored units; q is physical
+                const real wt = real(2) * w_of<real>(i) * real(Store<S>::kG);
+                q += (wt - real(2) * gv) * (real(1) / real(Store<S>::kG));
                 gv = wt - gv;
             }
         }
@@ -658,7 +712,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
             pull_any<real, S, PROB, FLOW>(a, x, y, f, g, q);
         }
         if (MODE == kFields) {
-            const Macro<real> m = cell_update<real, FLOW, false>(a, f, g);
+            const Macro<real> m = cell_update<real, S, FLOW, false>(a, f, g);
             const long long o = (long long)y * a.nx + x;
             if (a.oH) a.oH[o] = (double)m.H;
             if (a.oT) a.oT[o] = (double)m.T;
@@ -668,23 +722,22 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
             if (a.oRHO) a.oRHO[o] = (double)m.rho;
             continue;
         }
-        const Macro<real> m = cell_update<real, FLOW, true>(a, f, g);
+        const Macro<real> m = cell_update<real, S, FLOW, true>(a, f, g);
         E *d = static_cast<E *>(a.dst) + pop_index(x, y, 0, a.ny);
         if (!Store<S>::kSR || !(isfinite(m.H) && isfinite(m.rho))) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                Store<S>::stg_rn(d + (9 + i) * kTW, g[i]);
-                if (FLOW) Store<S>::stf_rn(d + i * kTW, f[i] - f_ofs<real, S>(i));
+                Store<S>::str_rn(d + (9 + i) * kTW, g[i]);
+                if (FLOW) Store<S>::str_rn(d + i * kTW, f[i]);
             }
         } else {
             uint32_t rs = hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x));
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 if (FLOW)
-                    Store<S>::st2(d + (9 + i) * kTW, d + i * kTW, g[i], f[i] - f_ofs<real, S>(i),
-                                  lcg_next32(rs));
+                    Store<S>::st2r(d + (9 + i) * kTW, d + i * kTW, g[i], f[i], lcg_next32(rs));
                 else
-                    Store<S>::stg(d + (9 + i) * kTW, g[i], lcg_next(rs));
+                    Store<S>::strs(d + (9 + i) * kTW, g[i], lcg_next(rs));
             }
         }
         if (MODE == kSweepDiag) {
