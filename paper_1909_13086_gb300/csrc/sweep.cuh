@@ -117,9 +117,12 @@ struct Store<double> {
 // float's bit pattern plus a uniform integer below the first discarded bit,
 // truncated toward zero, rounds the magnitude up with probability equal to the
 // discarded fraction (a carry into the exponent is the correct round-up).  r is
-// 16 random bits.  Only finite values may take this path (the sweep checks
-// each cell and stores a non-finite cell with the _rn encoders, so that NaN
-// stays NaN).
+// 16 random bits.  Only finite values may take this path (an infinity plus
+// random bits would become a NaN): the sweep uses it for single values, on
+// lattices without flow, and stores a non-finite cell there with the _rn
+// encoders.  The paired hardware conversion (cvt_rs_*) needs no such check: it
+// keeps NaN a NaN and an infinity an infinity, and rounds an FP16 overflow to
+// an infinity (checked on GB300 for NaN, +-Inf, +-7e4 and +-3e38).
 __device__ __forceinline__ float sr_add(float v, uint32_t add) {
     return __uint_as_float(__float_as_uint(v) + add);
 }
@@ -724,7 +727,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
         }
         const Macro<real> m = cell_update<real, S, FLOW, true>(a, f, g);
         E *d = static_cast<E *>(a.dst) + pop_index(x, y, 0, a.ny);
-        if (!Store<S>::kSR || !(isfinite(m.H) && isfinite(m.rho))) {
+        if (!Store<S>::kSR || (!FLOW && !(isfinite(m.H) && isfinite(m.rho)))) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 Store<S>::str_rn(d + (9 + i) * kTW, g[i]);

@@ -506,6 +506,24 @@ def test_16bit_round_to_nearest_stagnates(stream, prec):
 
 
 # ------------------------------------------------------------ extreme shapes
+@pytest.mark.parametrize("prec", ["fp16sr", "bf16sr"])
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_16bit_stochastic_rounding_keeps_non_finite_values(stream, prec, bad):
+    """The paired stochastic-rounding conversion stores a NaN or an infinity as
+    a non-finite value, so a diverging cell is still reported steps later."""
+    nx, ny, p = workloads.cavity_64x32()
+    lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+    lat.step(10)
+    f, g, step = lat.populations()
+    g[0, 12, 20] = bad
+    lat.set_populations(f, g, step)
+    lat.step(5)
+    d = lat.diagnostics(raise_on_diverged=False)
+    assert d["nan_flag"] == 1
+    f, g, _ = lat.populations()
+    assert not np.isfinite(g).all()
+
+
 @pytest.mark.parametrize("nx,ny,steps", [(2, 65535, 3), (262144, 2, 3), (129, 65535, 2)])
 def test_extreme_shapes_match_oracle(orc, stream, nx, ny, steps):
     """The tallest lattice the launch allows (65,535 rows: 65,535 blocks in y),
