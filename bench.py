@@ -18,6 +18,11 @@ all ranks / the slowest rank's time.
 
 --impl reference times the FP64 CPU oracle on this host's cores, one full
 oracle step of the same workload per step, and prints the same JSON line.
+
+--batch N times the batched path instead: N cavities of 256 x 128 (the
+serving size; Ra and strip centre varied, seeded) advanced together, one fused
+launch per step over all of them (graph-replayed); the last step carries the
+diagnostics.  Same JSON line, device-resident timing only.
 """
 from __future__ import annotations
 
@@ -118,15 +123,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_path(precision: str) -> str:
-    return os.path.join(ROOT, "profiles", f"sweep_{precision}_cavity_2048x1024.md")
+def profile_path(precision: str, batch: int = 0) -> str:
+    name = f"batch_{precision}_{batch}x256x128.md" if batch else f"sweep_{precision}_cavity_2048x1024.md"
+    return os.path.join(ROOT, "profiles", name)
 
 
-def profiled_traffic(precision: str = "fp32") -> float | None:
-    """DRAM bytes per launch of the sweep in `precision` from the committed
-    ncu summary, if it was taken on the current kernel source."""
+def profiled_traffic(precision: str = "fp32", batch: int = 0) -> float | None:
+    """DRAM bytes per launch of the sweep in `precision` (of the batch kernel
+    over `batch` lattices) from the committed ncu summary, if it was taken on
+    the current kernel source."""
     try:
-        text = open(profile_path(precision)).read()
+        text = open(profile_path(precision, batch)).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
@@ -375,6 +382,70 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+BATCH_NX, BATCH_NY = 256, 128
+
+
+def run_batch(args) -> None:
+    import numpy as np
+    import torch
+
+    from paper_1909_13086_gb300 import lbm, workloads
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec, n = args.precision, args.batch
+    rng = np.random.default_rng(7)
+    lats = [lbm.Lattice(BATCH_NX, BATCH_NY,
+                        workloads.params(Ra=float(rng.choice([1e6, 1e7, 1e8])),
+                                         strip_center=float(rng.choice([0.2, 0.35, 0.5, 0.65, 0.8])),
+                                         strip_width=0.25, seed=int(k)),
+                        precision=prec, stream=stream.cuda_stream) for k in range(n)]
+    b = lbm.Batch(n, stream.cuda_stream)
+    for lat in lats:
+        b.add(lat)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        start.record(stream)
+        b.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    elapsed = start.elapsed_time(stop) / 1e3
+    cells = n * BATCH_NX * BATCH_NY
+    kernel_s = elapsed / args.steps
+    alg_bytes = BYTES_PER_LUP[prec] * cells
+    peak, peak_kind = measured_peak_gbs()
+    achieved = alg_bytes / kernel_s / 1e9
+    nan = sum(lat.diagnostics(raise_on_diverged=False)["nan_flag"] for lat in lats)
+    assert nan == 0
+    line = {
+        "metric": METRIC, "value": round(cells * args.steps / elapsed / 1e6, 1), "unit": METRIC,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(kernel_s * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": f"batch of {n} cavities {BATCH_NX}x{BATCH_NY} (Ra 1e6-1e8, strip "
+                               f"W/4 at 0.2-0.8 W, seeded), {prec.upper()} populations, one fused "
+                               "launch per step", "lattices": n, "precision": prec,
+                   # both population buffers together are the algorithmic bytes of a step
+                   "l2": (f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB of populations), no flush"
+                          if alg_bytes > 129e6 else
+                          f"inputs fit in L2 ({alg_bytes / 1e6:.0f} MB of populations)")},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic(prec, n),
+                     "peak_source": f"{peak_kind} HBM copy bandwidth",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": None,
+        "gpu_launches": args.steps + 1,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    for lat in lats:
+        lat.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,11 +455,15 @@ def main(argv=None):
     ap.add_argument("--precision", choices=("fp32", "fp64", "fp16", "bf16", "fp16sr", "bf16sr"), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help=f"time a batch of this many {BATCH_NX}x{BATCH_NY} cavities instead")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch > 0:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -151,10 +151,11 @@ int lbm_set_diag_every(lbm_handle h, long long k);
  * sweeps lbm_step captures once into a CUDA graph and then replays (0 =
  * launch every sweep directly; default 128; up to 8 chunk graphs are cached
  * per handle, keyed by buffer parity and the position of the diagnostic
- * sweeps).  When the caller is itself capturing the
- * handle's stream, lbm_step launches directly.  Results do not depend on any
- * of these, except the rounding of the in-warp partial sums of the FP32
- * diagnostics.  Errors: LBM_ERR_ARG. */
+ * sweeps).  When the caller is itself capturing the handle's stream,
+ * lbm_step launches directly.  Results do not depend on any of these: the
+ * populations never, and the diagnostics of FP32 and 16-bit storage neither
+ * (their sums are exact fixed-point integer sums); the FP64 diagnostics sums
+ * follow the grouping of cells, to within FP64 rounding.  Errors: LBM_ERR_ARG. */
 int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int graph_chunk);
 
 /* Autotuner: times every launch shape of a small candidate set (rows per block
@@ -216,8 +217,11 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
  * tile in a device table), so lattices too small to fill the GPU alone -- the
  * 256 x 128 requests of a serving stream -- share it, and the per-step launch
  * cost is paid once.  The batch replays CUDA graphs of 64-step chunks (captured
- * once per batch composition).  Each step of a member computes exactly what
- * lbm_step would: the results are bitwise those of stepping it alone.
+ * once per batch composition) and uses its own launch shape (2 rows per block,
+ * 4 with 16-bit storage), whatever the members' lbm_set_launch settings.  Each
+ * step of a member computes exactly what lbm_step would: the populations are
+ * bitwise those of stepping it alone, and so are the diagnostics except on
+ * FP64 lattices (summation order, see lbm_set_launch).
  *
  * Members keep their own memory and state; lbm_diagnostics, lbm_read_fields
  * and friends keep working on them between batch steps.  Every member must

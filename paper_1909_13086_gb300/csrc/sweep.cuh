@@ -528,14 +528,14 @@ __device__ __forceinline__ void block_fold(T (&v)[NV], const int (&kind)[NV], vo
 }
 
 // ---- diagnostics accumulators ----
-// FP64 path: FP64 throughout.  FP32 path: each warp sums its cells in FP32,
-// then the warp partials are encoded as 64-bit fixed point (2^-24 units) and
-// every fold above the warp is an exact integer sum -- order-independent, and
-// on the integer pipes: on GB300 the FP64 rate (~2 FMA/clock/SM) makes FP64
-// shuffle folds cost as much as the sweep itself.  The maximum |u| travels as
-// the bit pattern of a non-negative float (integer order = float order).  The
-// record receives FP64 values decoded once at the end.  Range: totals up to
-// 2^39 (5.5e11) per quantity.
+// FP64 path: FP64 throughout.  FP32 path: each cell's f_l and H are encoded as
+// 64-bit fixed point (2^-24 units) and every sum from there on is an exact
+// integer sum -- independent of the order, so of the launch shape and of
+// batching, and on the integer pipes: on GB300 the FP64 rate (~2
+// FMA/clock/SM) makes FP64 shuffle folds cost as much as the sweep itself.
+// The maximum |u| travels as the bit pattern of a non-negative float (integer
+// order = float order).  The record receives FP64 values decoded once at the
+// end.  Range: totals up to 2^39 (5.5e11) per quantity.
 template <typename real>
 struct DiagAcc {
     using T = double;
@@ -558,14 +558,15 @@ __device__ __forceinline__ double dec_max(double v) { return v; }
 // record of 4 accumulators per block with plain stores -- no fence, no ticket,
 // so a block's lifetime does not grow -- and diag_reduce_kernel, launched
 // right after on the same stream, folds them into the FP64 record.  Inputs are
-// the thread's sums in the working precision.
+// the thread's sums of enc_sum(f_l) and enc_sum(H) over its cells.
 template <typename real>
-__device__ __forceinline__ void diag_partial(real sfl, real sH, real umax2, bool bad, double *dpart,
-                                             size_t bid, double *sh) {
+__device__ __forceinline__ void diag_partial(typename DiagAcc<real>::T sfl,
+                                             typename DiagAcc<real>::T sH, real umax2, bool bad,
+                                             double *dpart, size_t bid, double *sh) {
     using A = typename DiagAcc<real>::T;
-    const real wfl = warp_sum(sfl), wH = warp_sum(sH), wu = warp_max(umax2);
+    const real wu = warp_max(umax2);
     const int wbad = __any_sync(0xffffffffu, bad) ? 1 : 0;
-    A v[4] = {enc_sum(wfl), enc_sum(wH), enc_max(sqrt(wu)), A(wbad)};
+    A v[4] = {warp_sum(sfl), warp_sum(sH), enc_max(sqrt(wu)), A(wbad)};
     const int kind[4] = {0, 0, 1, 1};
     block_fold<4, A>(v, kind, sh);
     if (threadIdx.x == 0) {
@@ -702,8 +703,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
         iR = (lx == kTW - 1 && x < a.nx - 1) ? pop_index(x + 1, y0, 0, a.ny) - 1 : i0;
     }
 
-    real q = real(0);
-    real sfl = real(0), sH = real(0), umax2 = real(0);
+    real q = real(0), umax2 = real(0);
+    typename DiagAcc<real>::T sfl = 0, sH = 0;
     bool bad = false;
     for (int y = y0; y < y1; ++y, i0 += kRS, iL += kRS, iR += kRS) {
         if (!active) continue;
@@ -744,8 +745,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
             }
         }
         if (MODE == kSweepDiag) {
-            sfl += m.fl;
-            sH += m.H;
+            sfl += enc_sum(m.fl);
+            sH += enc_sum(m.H);
             umax2 = max(umax2, m.ux * m.ux + m.uy * m.uy);
             bad |= !(isfinite(m.H) && isfinite(m.rho));
         }
@@ -899,7 +900,7 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
     const int x = blockIdx.x * kTW + threadIdx.x;
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
-    real sfl = real(0), sH = real(0);
+    typename DiagAcc<real>::T sfl = 0, sH = 0;
     bool bad = false;
     if (x < a.nx) {
         for (int y = y0; y < y1; ++y) {
@@ -919,8 +920,8 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
                 Store<S>::stf_rn(dst + c + i * kTW, fi);
                 if (aux) Store<S>::stf_rn(aux + c + i * kTW, fi);
             }
-            sfl += fl;
-            sH += H;
+            sfl += enc_sum(fl);
+            sH += enc_sum(H);
             bad |= !isfinite(H);
         }
     }

@@ -65,7 +65,7 @@ def test_sweep_launch_count():
 def test_profiled_traffic_needs_matching_kernel_hash(tmp_path, monkeypatch):
     prof = tmp_path / "p.md"
     prof.write_text(f"kernel_source_sha256: {bench.kernel_source_hash()}\ndram_bytes_per_launch: 1.5e8\n")
-    monkeypatch.setattr(bench, "profile_path", lambda prec: str(prof))
+    monkeypatch.setattr(bench, "profile_path", lambda prec, batch=0: str(prof))
     assert bench.profiled_traffic() == 1.5e8
     prof.write_text("kernel_source_sha256: 0000000000000000\ndram_bytes_per_launch: 1.5e8\n")
     assert bench.profiled_traffic() is None
@@ -79,6 +79,10 @@ def test_profiled_traffic_is_per_precision(tmp_path, monkeypatch):
         f"kernel_source_sha256: {h}\ndram_bytes_per_launch: 2.5e8\n")
     assert bench.profiled_traffic("fp32") == 2.5e8
     assert bench.profiled_traffic("bf16sr") is None   # no summary for that precision
+    assert bench.profiled_traffic("fp32", 64) is None  # nor for the batch kernel
+    (tmp_path / "profiles" / "batch_fp32_64x256x128.md").write_text(
+        f"kernel_source_sha256: {h}\ndram_bytes_per_launch: 3.1e8\n")
+    assert bench.profiled_traffic("fp32", 64) == 3.1e8
 
 
 def test_committed_profiles_carry_hash_and_traffic():

@@ -85,6 +85,33 @@ def test_batch_membership_changes(stream):
         assert_same(state(ref), state(got))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_launch_shape_keeps_heated_wall_flux(stream, prec):
+    """Rows per block change the number of blocks that fold the heated-wall
+    inflow (row bands for the Stefan problem, tile columns for the cavity):
+    the flux stays that of the default shape -- exactly for the cavity, whose
+    heated wall is one row; to working-precision rounding for the Stefan
+    problem, whose heated column's rows a thread sums before the FP64 fold."""
+    cases = [(128, 4, workloads.stefan_1024x4(nx=128)[2]),
+             (300, 77, workloads.params(Ra=1e6, strip_center=0.4))]
+    for nx, ny, p in cases:
+        tol = 1e-12 if prec == "fp64" or p["problem"] == lbm.LBM_CAVITY else 1e-6
+        ref = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+        ref.step(40)
+        lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
+        lbm.lbm_set_launch(lat.h, 3, 4, 16)
+        lat.step(40)
+        fr, gr, sr, dr = state(ref)
+        fl, gl, sl, dl = state(lat)
+        assert sr == sl and np.array_equal(fr, fl) and np.array_equal(gr, gl)
+        for k in ("Q_strip", "Q_cum", "Nu"):
+            assert dl[k] == pytest.approx(dr[k], rel=tol, abs=1e-14), (nx, k)
+        if prec == "fp32":
+            assert dl["melt_fraction"] == dr["melt_fraction"] and dl["H_total"] == dr["H_total"]
+            if p["problem"] == lbm.LBM_CAVITY:
+                assert dl == dr
+
+
 def test_batch_rejects_mixed_members(stream):
     b = lbm.Batch(2, stream)
     b.add(make(stream, "fp32", 64, 32, {}))
@@ -109,15 +136,12 @@ def test_autotune_leaves_state_and_caches(stream):
     other = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
     t2 = lbm.lbm_autotune(other.h, 50)
     assert t2["us_per_step"] == 0.0 and (t2["rows"], t2["prefetch"]) == (t1["rows"], t1["prefetch"])
-    # a tuned lattice computes exactly what an untuned one does (the in-warp
-    # FP32 partial sums of the diagnostics may group cells differently)
+    # a tuned lattice computes exactly what an untuned one does, diagnostics
+    # included (FP32 sums are exact fixed-point sums, independent of grouping)
     ref = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
     ref.step(60)
     lat.step(50)
-    fr, gr, sr, dr = state(ref)
-    fl, gl, sl, dl = state(lat)
-    assert sr == sl and np.array_equal(fr, fl) and np.array_equal(gr, gl)
-    assert dl["melt_fraction"] == pytest.approx(dr["melt_fraction"], rel=1e-6, abs=1e-12)
+    assert_same(state(ref), state(lat))
 
 
 @pytest.mark.parametrize("batched", [False, True])
