@@ -830,6 +830,7 @@ struct lbm_batch_s {
     std::vector<int> host_starts;
     std::vector<int> host_parity;
     int nblocks = 0;
+    int uniform = 0;          // blocks per member when all members have the same count
     bool dirty = true;        // table must be rebuilt and uploaded
     int precision = -1, problem = -1, flow = -1;
     int graph_chunk = 64;     // even: parities return to their start value
@@ -882,6 +883,7 @@ void batch_build(lbm_batch_s *b) {
     const size_t eb = entry_bytes<real>();
     b->host_entries.assign(eb * b->members.size(), 0);
     b->host_starts.assign(b->members.size(), 0);
+    b->uniform = 0;
     int start = 0;
     for (size_t r = 0; r < b->members.size(); ++r) {
         lbm_s *h = b->members[r];
@@ -899,6 +901,8 @@ void batch_build(lbm_batch_s *b) {
         b->host_starts[r] = start;
         e.gx = (int)h->grid.x;
         e.gy = gy;
+        const int nb = e.gx * e.gy;
+        b->uniform = r == 0 ? nb : (b->uniform == nb ? nb : 0);
         start += e.gx * e.gy;
         std::memcpy(b->host_entries.data() + r * eb, &e, eb);
     }
@@ -931,8 +935,8 @@ int batch_steps(lbm_batch_s *b, long long n) {
             BATCH_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
             for (int j = 0; j < K && e == cudaSuccess; ++j)
-                e = launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->nblocks, b->problem,
-                                          b->flow != 0, false, j, b->stream);
+                e = launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->uniform, b->nblocks,
+                                          b->problem, b->flow != 0, false, j, b->stream);
             cudaGraph_t g = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
             if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -952,8 +956,8 @@ int batch_steps(lbm_batch_s *b, long long n) {
     }
     for (; done < n; ++done) {
         const cudaError_t e =
-            launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->nblocks, b->problem, b->flow != 0,
-                                  done == n - 1, (int)(done & 1), b->stream);
+            launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->uniform, b->nblocks, b->problem,
+                                  b->flow != 0, done == n - 1, (int)(done & 1), b->stream);
         if (e != cudaSuccess) return batch_err(LBM_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
     }
     for (lbm_s *h : b->members) {

@@ -812,7 +812,9 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
 // parity[r] ^ (j & 1).  The block's start-up is two dependent reads: the
 // search over the compact starts array (its first lines stay in L1 for the
 // blocks an SM runs), then the whole entry, copied into shared memory 16 bytes
-// per thread, alongside the parity word.
+// per thread, alongside the parity word.  When every entry has the same number
+// of blocks (`uniform`; a serving group's lattices share one size) the entry
+// is blockIdx.x / uniform and the search and its barrier are skipped.
 __device__ __forceinline__ int batch_find(const int *starts, int n, int b) {
     int lo = 0, hi = n - 1;  // last entry with starts[r] <= b
     while (lo < hi) {
@@ -825,14 +827,19 @@ __device__ __forceinline__ int batch_find(const int *starts, int n, int b) {
 template <typename real, typename S, int PROB, bool FLOW, int MODE>
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     batch_kernel(const BatchEntry<real> *entries, const int *starts, const int *parity, int n,
-                 int j) {
+                 int uniform, int j) {
     static_assert(sizeof(BatchEntry<real>) % 16 == 0, "entries are copied in 16-byte pieces");
     __shared__ double sh[32 * 4];
     __shared__ __align__(16) unsigned char entry_sh[sizeof(BatchEntry<real>)];
     __shared__ int meta[2];
-    if (threadIdx.x == 0) meta[0] = batch_find(starts, n, blockIdx.x);
-    __syncthreads();
-    const int r = meta[0];
+    int r;
+    if (uniform > 0) {
+        r = (int)(blockIdx.x / (unsigned)uniform);
+    } else {
+        if (threadIdx.x == 0) meta[0] = batch_find(starts, n, blockIdx.x);
+        __syncthreads();
+        r = meta[0];
+    }
     const int4 *s4 = reinterpret_cast<const int4 *>(entries + r);
     int4 *d4 = reinterpret_cast<int4 *>(entry_sh);
     for (unsigned k = threadIdx.x; k < sizeof(BatchEntry<real>) / 16; k += blockDim.x)
@@ -1033,15 +1040,17 @@ cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int
 
 template <typename real, typename S>
 cudaError_t launch_batch(const void *entries, const int *starts, const int *parity, int n,
-                         int nblocks, int problem, bool flow, bool diag, int j, cudaStream_t s) {
+                         int uniform, int nblocks, int problem, bool flow, bool diag, int j,
+                         cudaStream_t s) {
     const BatchEntry<real> *e = static_cast<const BatchEntry<real> *>(entries);
     const dim3 grid(nblocks), block(kTW);
-#define BTRIRT_BATCH(PROB, FLOW)                                                                   \
-    if (diag)                                                                                      \
-        batch_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(e, starts, parity, n, \
-                                                                             j);                   \
-    else                                                                                           \
-        batch_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(e, starts, parity, n, j);
+#define BTRIRT_BATCH(PROB, FLOW)                                                                 \
+    if (diag)                                                                                    \
+        batch_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(e, starts, parity,  \
+                                                                             n, uniform, j);     \
+    else                                                                                         \
+        batch_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(e, starts, parity, n,   \
+                                                                         uniform, j);
     if (problem == kCavity) {
         if (flow) { BTRIRT_BATCH(kCavity, true) } else { BTRIRT_BATCH(kCavity, false) }
     } else {
@@ -1093,6 +1102,6 @@ cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, 
                                                  cudaStream_t);                                  \
     template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t); \
     template cudaError_t launch_batch<REAL, S>(const void *, const int *, const int *, int, int,  \
-                                               int, bool, bool, int, cudaStream_t);
+                                               int, int, bool, bool, int, cudaStream_t);
 
 }  // namespace btrirt
