@@ -325,6 +325,39 @@ def test_torch_allocator_hook(orc, stream):
         lbm.use_default_allocator()
 
 
+def test_allocation_failure_is_reported(stream):
+    """An allocator that refuses every request (a full device or a spent arena)
+    makes lbm_create and lbm_batch_create fail with LBM_ERR_OOM; nothing is
+    freed that was not allocated, and the library works again once the default
+    allocator is back."""
+    asked, freed = [], []
+
+    def _alloc(nbytes, ctx):
+        asked.append(nbytes)
+        return None
+
+    def _free(ptr, ctx):
+        freed.append(ptr)
+
+    hooks = (lbm.ALLOC_FN(_alloc), lbm.FREE_FN(_free))
+    lbm._check(lbm.lib().lbm_set_allocator(hooks[0], hooks[1], None))
+    try:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(64, 32, lbm.PRECISIONS["fp32"], stream)
+        assert e.value.status == lbm.LBM_ERR_OOM and asked
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_batch_create(4, stream)
+        assert e.value.status == lbm.LBM_ERR_OOM
+        assert freed == []
+    finally:
+        lbm.use_default_allocator()
+    nx, ny, p = workloads.cavity_64x32()
+    lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    lat.step(10)
+    assert lat.diagnostics()["step"] == 10
+    lat.close()
+
+
 # ------------------------------------------------------------ full size
 def test_full_size_sampled_parity_fp32(orc, stream):
     """2048 x 1024 production cavity, FP32, the benchmark's launch shape: one
