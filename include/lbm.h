@@ -104,7 +104,9 @@ typedef struct {
     double heated_len;       /* b - a (cavity) or ny (Stefan)                            */
 } lbm_derived;
 
-/* Diagnostics of the current step, accumulated in FP64 on the device. */
+/* Diagnostics of the current step, reduced on the device: sums over cells in
+ * FP64 for LBM_FP64 lattices, exactly in 64-bit fixed point (2^-24 units, each
+ * cell's value rounded once) for FP32 and 16-bit storage; delivered as FP64. */
 typedef struct {
     long long step;          /* steps taken since lbm_set_params                        */
     double melt_fraction;    /* sum f_l / (nx ny)                                        */
