@@ -240,7 +240,9 @@ def run_reference(args) -> None:
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config("fp64"),
+        # the same workload and config as this arm's GPU line; the oracle
+        # computes it in FP64 (dtype)
+        "config": workload_config(args.precision),
         "cpu_baseline": {"value": round(rate, 3), "unit": METRIC, "cores": threads,
                          "kind": "oracle",
                          "sample": f"{n} full FP64 oracle steps of the {NX}x{NY} cavity"},

@@ -113,3 +113,23 @@ def test_clock_summary_parses_nvidia_smi_csv(tmp_path):
     s = cs.summary()
     assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
     assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_reference_arm_line(capsys, monkeypatch):
+    """--impl reference times the oracle on this host and prints the contract's
+    line with the GPU arm's config; ranks other than 0 print nothing."""
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "MLUPS" and line["value"] > 0
+    assert line["config"] == bench.workload_config("fp32")
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["warmup"] == 3
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "MLUPS",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert capsys.readouterr().out.strip() == ""
