@@ -67,8 +67,12 @@ struct F16 {};
 template <bool SR>
 struct BF16 {};
 
-// Each codec decodes / encodes an f plane (ldf / stf: the stored value is
-// f_i - w_i for the 16-bit codecs, see f_ofs) or a g plane (ldg / stg).
+// Each codec has two faces.  Physical values, for set-up and read-back: ldf /
+// stf_rn decode / encode an f plane (the stored value is f_i - w_i for the
+// 16-bit codecs, see f_ofs), ldg / stg_rn a g plane.  Stored units, for the
+// sweep (see ld_f): ldr reads a value as stored, str_rn / strs / st2r write
+// one rounded to nearest, one stochastically, or a (g_i, f_i - w_i) pair
+// stochastically.
 template <typename S>
 struct Store;
 template <>
@@ -77,11 +81,8 @@ struct Store<float> {
     static constexpr bool kDev = false, kSR = false;
     __device__ static float ldf(const float *p) { return __ldg(p); }
     __device__ static float ldg(const float *p) { return __ldg(p); }
-    __device__ static void stf(float *p, float v, uint32_t) { *p = v; }
-    __device__ static void stg(float *p, float v, uint32_t) { *p = v; }
     __device__ static void stf_rn(float *p, float v) { *p = v; }
     __device__ static void stg_rn(float *p, float v) { *p = v; }
-    __device__ static void st2(float *pg, float *pf, float g, float f, uint32_t) { *pg = g; *pf = f; }
     // stored units (see the 16-bit codecs): the values themselves
     static constexpr float kF = 1.0f, kG = 1.0f;
     __device__ static float ldr(const float *p) { return __ldg(p); }
@@ -95,14 +96,8 @@ struct Store<double> {
     static constexpr bool kDev = false, kSR = false;
     __device__ static double ldf(const double *p) { return __ldg(p); }
     __device__ static double ldg(const double *p) { return __ldg(p); }
-    __device__ static void stf(double *p, double v, uint32_t) { *p = v; }
-    __device__ static void stg(double *p, double v, uint32_t) { *p = v; }
     __device__ static void stf_rn(double *p, double v) { *p = v; }
     __device__ static void stg_rn(double *p, double v) { *p = v; }
-    __device__ static void st2(double *pg, double *pf, double g, double f, uint32_t) {
-        *pg = g;
-        *pf = f;
-    }
     static constexpr double kF = 1.0, kG = 1.0;
     __device__ static double ldr(const double *p) { return __ldg(p); }
     __device__ static void str_rn(double *p, double v) { *p = v; }
@@ -156,14 +151,8 @@ struct Store<F16<SR>> {
     }
     __device__ static float ldf(const __half *p) { return __half2float(__ldg(p)) * (1.0f / kF); }
     __device__ static float ldg(const __half *p) { return __half2float(__ldg(p)) * (1.0f / kG); }
-    __device__ static void stf(__half *p, float v, uint32_t r) { enc(p, v * kF, r); }
-    __device__ static void stg(__half *p, float v, uint32_t r) { enc(p, v * kG, r); }
     __device__ static void stf_rn(__half *p, float v) { *p = __float2half_rn(v * kF); }
     __device__ static void stg_rn(__half *p, float v) { *p = __float2half_rn(v * kG); }
-    // g_i and f_i - w_i of one cell, stochastically rounded together (SR only)
-    __device__ static void st2(__half *pg, __half *pf, float g, float f, uint32_t rbits) {
-        st2r(pg, pf, g * kG, f * kF, rbits);
-    }
     // stored units: g_i kG and (f_i - w_i) kF, converted without scaling
     __device__ static float ldr(const __half *p) { return __half2float(__ldg(p)); }
     __device__ static void str_rn(__half *p, float v) { *p = __float2half_rn(v); }
@@ -186,14 +175,8 @@ struct Store<BF16<SR>> {
     }
     __device__ static float ldf(const __nv_bfloat16 *p) { return ld(p); }
     __device__ static float ldg(const __nv_bfloat16 *p) { return ld(p); }
-    __device__ static void stf(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
-    __device__ static void stg(__nv_bfloat16 *p, float v, uint32_t r) { st(p, v, r); }
     __device__ static void stf_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static void stg_rn(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
-    __device__ static void st2(__nv_bfloat16 *pg, __nv_bfloat16 *pf, float g, float f,
-                               uint32_t rbits) {
-        st2r(pg, pf, g, f, rbits);
-    }
     // stored units: g_i and f_i - w_i (no scaling)
     static constexpr float kF = 1.0f, kG = 1.0f;
     __device__ static float ldr(const __nv_bfloat16 *p) { return ld(p); }
