@@ -71,39 +71,87 @@ _D9 = ctypes.c_double * 9
 _I9 = ctypes.c_int * 9
 
 
+def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
+    """Declare the C signatures of an oracle library (the built one, or a
+    variant compiled by ``compile_variant``)."""
+    L.orc_splitmix64.restype = ctypes.c_uint64
+    L.orc_splitmix64.argtypes = [ctypes.c_uint64]
+    L.orc_invert.argtypes = [ctypes.c_double, ctypes.c_double, _D, _D]
+    L.orc_geq.argtypes = [ctypes.c_double] * 4 + [_D]
+    L.orc_g_collide.argtypes = [_D] + [ctypes.c_double] * 7 + [_D]
+    L.orc_feq.argtypes = [ctypes.c_double] * 3 + [_D]
+    L.orc_f_collide.argtypes = [_D] + [ctypes.c_double] * 8 + [_D]
+    L.orc_stefan_lambda.restype = ctypes.c_double
+    L.orc_stefan_lambda.argtypes = [ctypes.c_double]
+    L.orc_neumann_T.restype = ctypes.c_double
+    L.orc_neumann_T.argtypes = [ctypes.c_double] * 6
+    L.orc_derive.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params),
+                             ctypes.POINTER(Derived)]
+    L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params),
+                             ctypes.POINTER(ctypes.c_void_p)]
+    L.orc_destroy.argtypes = [ctypes.c_void_p]
+    L.orc_destroy.restype = None
+    L.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+    L.orc_fields.argtypes = [ctypes.c_void_p] + [_D] * 6
+    L.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(Diag)]
+    L.orc_get_derived.argtypes = [ctypes.c_void_p, ctypes.POINTER(Derived)]
+    L.orc_get_populations.argtypes = [ctypes.c_void_p, _D, _D]
+    L.orc_set_populations.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_longlong]
+    L.orc_cell_update.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_int, ctypes.c_int,
+                                  _D, _D, _D, _D]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        L.orc_splitmix64.restype = ctypes.c_uint64
-        L.orc_splitmix64.argtypes = [ctypes.c_uint64]
-        L.orc_invert.argtypes = [ctypes.c_double, ctypes.c_double, _D, _D]
-        L.orc_geq.argtypes = [ctypes.c_double] * 4 + [_D]
-        L.orc_g_collide.argtypes = [_D] + [ctypes.c_double] * 7 + [_D]
-        L.orc_feq.argtypes = [ctypes.c_double] * 3 + [_D]
-        L.orc_f_collide.argtypes = [_D] + [ctypes.c_double] * 8 + [_D]
-        L.orc_stefan_lambda.restype = ctypes.c_double
-        L.orc_stefan_lambda.argtypes = [ctypes.c_double]
-        L.orc_neumann_T.restype = ctypes.c_double
-        L.orc_neumann_T.argtypes = [ctypes.c_double] * 6
-        L.orc_derive.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params),
-                                 ctypes.POINTER(Derived)]
-        L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params),
-                                 ctypes.POINTER(ctypes.c_void_p)]
-        L.orc_destroy.argtypes = [ctypes.c_void_p]
-        L.orc_destroy.restype = None
-        L.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
-        L.orc_fields.argtypes = [ctypes.c_void_p] + [_D] * 6
-        L.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(Diag)]
-        L.orc_get_derived.argtypes = [ctypes.c_void_p, ctypes.POINTER(Derived)]
-        L.orc_get_populations.argtypes = [ctypes.c_void_p, _D, _D]
-        L.orc_set_populations.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_longlong]
-        L.orc_cell_update.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_int, ctypes.c_int,
-                                      _D, _D, _D, _D]
-        _lib = L
+        _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+# ------------------------------------------------------ planted mistakes
+# A pin is only worth something if a plausible slip in the oracle breaks it.
+# The tests check that by compiling copies of lbm_oracle.c with one mistake
+# planted (a text replacement) and running the pin against the copy.
+def compile_variant(replacements: list[tuple[str, str]], out_dir: str) -> str:
+    """Compile a copy of lbm_oracle.c with each (old, new) replacement applied
+    (each ``old`` must occur exactly once) into out_dir; returns the library
+    path."""
+    src = open(_SRC).read()
+    for old, new in replacements:
+        if src.count(old) != 1:
+            raise ValueError(f"replacement target must occur once: {old!r}")
+        src = src.replace(old, new)
+    os.makedirs(out_dir, exist_ok=True)
+    csrc = os.path.join(out_dir, "lbm_oracle_variant.c")
+    with open(csrc, "w") as fh:
+        fh.write(src)
+    so = os.path.join(out_dir, "liboracle_variant.so")
+    cmd = compile_cmd()
+    cmd[cmd.index(_SRC)] = csrc
+    cmd[cmd.index(_LIB)] = so
+    subprocess.run(cmd + ["-I", _HERE], check=True)
+    return so
+
+
+class variant:
+    """Context manager: every function of this module uses the library at
+    ``path`` (a planted-mistake copy) instead of the oracle, until exit."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        _lib = _bind(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
 
 
 def _ptr(a: np.ndarray | None):

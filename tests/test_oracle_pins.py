@@ -5,9 +5,13 @@ plausible slip (a dropped term, a wrong sign or index, a transposed operand)
 would break -- moment identities (Eq. 4), the moment-space form of the block
 collision (Eq. 2, "can be written as an MRT form"), the SRT/BGK reduction,
 Guo's forcing, conservation in a closed box, the exact enthalpy budget, the
-Neumann solution (Eqs. 7-8), the one-cell interface of Eq. 6, mirror symmetry,
-the diffusivity of Eq. 5, hydrostatic balance, and published generator
-outputs.
+Neumann solution (Eqs. 7-8) for the front, the profile and the heated-wall
+flux (hence Q and Nu), the one-cell interface of Eq. 6, mirror symmetry, the
+diffusivity of Eq. 5, the viscosity of the flow operator (a decaying shear
+wave at Pr != 1), the solid treatment u = f_l u*, hydrostatic balance, the
+distribution of the seeded initial perturbation, and published generator
+outputs.  The last test plants such slips in copies of the oracle and checks
+that the matching pins fail on them.
 """
 import math
 import os
@@ -504,3 +508,240 @@ def test_srt_leaks_into_solid_when_k_not_1(orc, k):
         assert mushy.sum(axis=1).min() >= 2
     else:
         assert H.min() < -1e-6
+
+
+# ------------------------------------------- flow viscosity (reading A2)
+def check_shear_wave_decays_at_nu(orc):
+    """A shear wave u_y = U sin(2 pi (x + 1/2)/nx) in liquid at rest between the
+    no-slip side walls (an eigenmode of the viscous term that vanishes on both
+    half-way walls and carries no net flux) decays as exp(-nu k^2 t): the flow
+    operator's second-moment rate k2f = 1/(nu/c_s^2 + 1/2) sets the kinematic
+    viscosity, as Eq. 5 does for the diffusivity.  Pr = 6.2, so nu = 6.2 alpha
+    and a rate taken from alpha would decay six times slower.  No buoyancy
+    (Ra = 0), no heated wall; the box is tall so that the top and bottom walls
+    do not reach the measured middle rows in 300 steps."""
+    nx, ny, Pr, nu, U = 32, 512, 6.2, 0.1, 1e-3
+    o = orc.Oracle(nx, ny, threads=4, Ra=0.0, Pr=Pr, Ste=1.0, alpha_override=nu / Pr,
+                   strip_width=0.0, init_amp=0.0)
+    x = np.arange(nx) + 0.5
+    kw = 2.0 * math.pi / nx
+    f = np.empty((9, ny, nx))
+    g = np.empty((9, ny, nx))
+    for xx in range(nx):
+        uy = U * math.sin(kw * x[xx])
+        f[:, :, xx] = orc.feq(1.0, 0.0, uy)[:, None]
+        g[:, :, xx] = orc.geq(1.5, 0.5, 0.0, uy)[:, None]   # liquid: H > L = 1
+    o.set_populations(f, g)
+    n = 300
+    o.step(n)
+    F = o.fields()
+    assert F["fl"].min() == 1.0
+    mid = F["uy"][ny // 2 - 16: ny // 2 + 16].mean(axis=0)
+    amp = 2.0 / nx * np.sum(mid * np.sin(kw * x))
+    decay = math.exp(-nu * kw * kw * n)
+    assert amp == pytest.approx(U * decay, rel=1e-2)
+    # the largest speed is at least the wave's crest in the middle rows and a
+    # little more where the flow turns at the top and bottom walls (about 7 %
+    # here); |u_x| alone or |u|^2 would be far off
+    crest = U * np.sin(kw * x).max() * decay
+    assert 0.99 * crest <= o.diagnostics()["max_u"] <= 1.15 * crest
+
+
+def test_shear_wave_decays_at_the_flow_viscosity(orc):
+    check_shear_wave_decays_at_nu(orc)
+
+
+# ------------------------------------------ solid treatment (reading A3)
+def check_velocity_is_fl_times_ustar(orc):
+    """u = f_l u*, u* = (j + F/2)/rho: zero in every solid cell, u* itself in
+    every liquid cell, f_l u* in the mushy ones.  u* is formed here from the
+    populations streamed by hand (interior cells, no wall) and the force
+    F = g beta (T - T_m) y of the enthalpy streamed the same way, T taken from
+    Eq. 1's definition of H."""
+    nx, ny, Lh = 40, 24, 1.0
+    o = orc.Oracle(nx, ny, Ra=1e6, Pr=0.7, Ste=1.0 / Lh, strip_width=0.0, init_amp=0.0)
+    gbeta = o.derived()["gbeta"]
+    cx, cy, _, _ = orc.lattice()
+    rng = np.random.default_rng(5)
+    H = rng.uniform(-0.6, 1.6, (ny, nx))    # solid, mushy and liquid cells
+    f = np.empty((9, ny, nx))
+    g = np.empty((9, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            u = rng.uniform(-0.05, 0.05, 2)
+            T0 = min(H[y, x], 0.0) + max(H[y, x] - Lh, 0.0)
+            g[:, y, x] = orc.geq(H[y, x], T0, 0.0, 0.0) + 0.01 * (rng.random(9) - 0.5)
+            f[:, y, x] = orc.feq(1.0 + 0.02 * (rng.random() - 0.5), u[0], u[1]) \
+                + 0.002 * (rng.random(9) - 0.5)
+    o.set_populations(f, g)
+    o.step(1)
+    F = o.fields()
+    fs = np.stack([f[i, 1 - cy[i]: ny - 1 - cy[i], 1 - cx[i]: nx - 1 - cx[i]] for i in range(9)])
+    gs = np.stack([g[i, 1 - cy[i]: ny - 1 - cy[i], 1 - cx[i]: nx - 1 - cx[i]] for i in range(9)])
+    rho = fs.sum(0)
+    jx = np.tensordot(cx, fs, 1)
+    jy = np.tensordot(cy, fs, 1)
+    Hs = gs.sum(0)
+    T = np.minimum(Hs, 0.0) + np.maximum(Hs - Lh, 0.0)
+    fl = np.clip(Hs / Lh, 0.0, 1.0)
+    usx, usy = jx / rho, (jy + 0.5 * gbeta * T) / rho
+    ux, uy = F["ux"][1:-1, 1:-1], F["uy"][1:-1, 1:-1]
+    solid, liquid = fl == 0.0, fl == 1.0
+    mushy = ~solid & ~liquid
+    assert solid.sum() > 100 and liquid.sum() > 100 and mushy.sum() > 100
+    assert np.array_equal(F["fl"][1:-1, 1:-1], fl)
+    assert np.all(ux[solid] == 0.0) and np.all(uy[solid] == 0.0)
+    # the half-force shift is ~3e-5 here, so 1e-15 separates u* from j/rho
+    assert np.abs(ux[liquid] - usx[liquid]).max() <= 1e-15
+    assert np.abs(uy[liquid] - usy[liquid]).max() <= 1e-15
+    assert np.abs(uy[mushy] - fl[mushy] * usy[mushy]).max() <= 1e-15
+    assert np.abs(usy[liquid]).max() > 1e-2   # the liquid does move
+
+
+def test_velocity_is_liquid_fraction_times_ustar(orc):
+    check_velocity_is_fl_times_ustar(orc)
+
+
+# --------------------------------- heated-wall inflow and Nu (reading A17)
+def neumann_wall_flux(orc, Ste, alpha, n):
+    """Heat flux per unit wall length at time n of the Neumann solution
+    (Eqs. 7-8): -alpha dT/dx at x = 0 = alpha dT / (erf(lambda) sqrt(pi alpha t))."""
+    lam = orc.stefan_lambda(Ste)
+    return alpha * 1.0 / (math.erf(lam) * math.sqrt(math.pi * alpha * n))
+
+
+WALL_FLUX_CASES = [  # (problem, Ste, checkpoints, tolerance)
+    ("stefan", 1.0, (2000, 8000), 1e-2),
+    ("stefan", 0.1, (8000,), 3e-2),
+    ("cavity", 1.0, (2000, 6000), 1e-2),
+]
+
+
+def check_wall_flux_and_nu(orc, problem, Ste, steps, tol):
+    """The inflow the oracle reports for a step, Q = sum over heated crossings
+    of (2 w_i T_h - 2 g*_opp), is the heat entering through the T_h wall: for
+    one-phase melting from a wall held at T_h it follows Neumann's flux times
+    the wall length.  Stefan problem: left wall, ny cells long, Nu = Q nx /
+    (alpha dT ny).  Cavity with its whole bottom wall heated and the flow off:
+    the same solution along y, the wall nx cells long, Nu = Q ny / (alpha dT
+    nx) (reference length = cavity height)."""
+    alpha = 1.0 / 6.0
+    if problem == "stefan":
+        nx, ny = 256, 4
+        o = orc.Oracle(nx, ny, problem=orc.STEFAN, Ste=Ste, flow_on=0, alpha_override=alpha,
+                       k0=1.0, k2=-1.0, init_amp=0.0)
+        wall, href = ny, nx
+    else:
+        # wide enough that the two side-wall columns, where half-way
+        # bounce-back of the diagonal populations is not a mirror image,
+        # shift the total by well under the gate
+        nx, ny = 64, 160
+        o = orc.Oracle(nx, ny, threads=4, problem=orc.CAVITY, Ste=Ste, flow_on=0,
+                       alpha_override=alpha, strip_center=0.5, strip_width=1.0, k0=1.0,
+                       k2=-1.0, init_amp=0.0)
+        wall, href = nx, ny
+    done = 0
+    for n in steps:
+        o.step(n - done)
+        done = n
+        d = o.diagnostics()
+        q = neumann_wall_flux(orc, Ste, alpha, n)
+        assert d["Q_strip"] == pytest.approx(q * wall, rel=tol), (problem, n)
+        assert d["Nu"] == pytest.approx(q * wall * href / (alpha * wall), rel=tol), (problem, n)
+
+
+@pytest.mark.parametrize("problem,Ste,steps,tol", WALL_FLUX_CASES)
+def test_heated_wall_flux_and_nusselt_follow_neumann(orc, problem, Ste, steps, tol):
+    check_wall_flux_and_nu(orc, problem, Ste, steps, tol)
+
+
+# ------------------------------------------ initial state (reading A15)
+def test_initial_perturbation_is_uniform_on_plus_minus_amp(orc):
+    """H0 = amp (2r - 1) with r uniform on [0, 1): inside [-amp, amp], mean
+    zero and uniform (Kolmogorov-Smirnov), no two neighbouring cells alike;
+    cells with H0 > 0 are mushy at T_m, the others subcooled solid, f at rest."""
+    from scipy import stats
+    amp = 1e-3
+    o = orc.Oracle(256, 128, Ra=1e6, init_amp=amp, seed=3)
+    F = o.fields()
+    H = F["H"].ravel()
+    assert H.min() >= -amp and H.max() < amp
+    assert abs(H.mean()) < 4 * amp / math.sqrt(3 * H.size)
+    assert stats.kstest(H, stats.uniform(loc=-amp, scale=2 * amp).cdf).pvalue > 1e-3
+    assert np.all(F["H"][:, 1:] != F["H"][:, :-1]) and np.all(F["H"][1:] != F["H"][:-1])
+    assert np.all(F["T"][F["H"] > 0] == 0.0) and np.all(F["fl"][F["H"] <= 0] == 0.0)
+    assert np.array_equal(F["T"][F["H"] <= 0], F["H"][F["H"] <= 0])
+    assert np.all(F["rho"] == 1.0) and np.all(F["ux"] == 0.0) and np.all(F["uy"] == 0.0)
+    f, _ = o.populations()
+    _, _, w, _ = orc.lattice()
+    assert np.array_equal(f, np.broadcast_to(w[:, None, None], f.shape))
+    other = orc.Oracle(256, 128, Ra=1e6, init_amp=amp, seed=4).fields()["H"]
+    assert np.abs(other - F["H"]).max() > amp   # the seed matters
+
+
+def test_nan_flag_marks_a_non_finite_cell(orc):
+    o = orc.Oracle(40, 20, Ra=1e5)
+    o.step(3)
+    assert o.diagnostics()["nan_flag"] == 0.0
+    f, g = o.populations()
+    g[4, 7, 11] = np.nan
+    o.set_populations(f, g, 3)
+    o.step(1)
+    assert o.diagnostics()["nan_flag"] == 1.0
+
+
+# ------------------------------------------------- planted mistakes
+# Each pin above must fail on an oracle with the matching plausible slip.
+MUTATIONS = {
+    "k2f from alpha": (
+        [("d->k2f = 1.0 / (d->nu / CS2 + 0.5);", "d->k2f = 1.0 / (d->alpha / CS2 + 0.5);")],
+        [check_shear_wave_decays_at_nu]),
+    "f_l factor dropped": (
+        [("ux = fl * (jx + 0.5 * Fx) / rho;", "ux = (jx + 0.5 * Fx) / rho;"),
+         ("uy = fl * (jy + 0.5 * Fy) / rho;", "uy = (jy + 0.5 * Fy) / rho;")],
+        [check_velocity_is_fl_times_ustar]),
+    "half-force shift dropped": (
+        [("uy = fl * (jy + 0.5 * Fy) / rho;", "uy = fl * jy / rho;")],
+        [check_velocity_is_fl_times_ustar]),
+    "Href and heated length swapped in Nu": (
+        [("s->Q_last * s->d.Href / (s->d.alpha * RHO0 * CP * (TH - TM) * s->d.heated_len)",
+          "s->Q_last * s->d.heated_len / (s->d.alpha * RHO0 * CP * (TH - TM) * s->d.Href)")],
+        [lambda orc: check_wall_flux_and_nu(orc, *WALL_FLUX_CASES[0]),
+         lambda orc: check_wall_flux_and_nu(orc, *WALL_FLUX_CASES[2])]),
+    "inflow counted once instead of twice": (
+        [("qin += 2.0 * W[i] * CP * TH - 2.0 * gprev[ko];", "qin += W[i] * CP * TH - gprev[ko];")],
+        [lambda orc: check_wall_flux_and_nu(orc, *WALL_FLUX_CASES[0])]),
+    # and some older pins, each against the slip it is meant to catch
+    "Eq. 4 rest term w_0 C_p T dropped": (
+        [("out[0] = H - CP * T + W[0] * CP * T;", "out[0] = H - CP * T;")],
+        [test_geq_moments]),
+    "Eq. 2 k1 and k2 exchanged": (
+        [("out[i] = p[i] - k0 * n[i] - (k1 - k0) * W[i] * cM1 / CS2 -\n"
+          "                 (k2 - k0) * W[i] * q_contract(i, M2) / (2.0 * CS2 * CS2);",
+          "out[i] = p[i] - k0 * n[i] - (k2 - k0) * W[i] * cM1 / CS2 -\n"
+          "                 (k1 - k0) * W[i] * q_contract(i, M2) / (2.0 * CS2 * CS2);")],
+        [test_g_collision_is_block_relaxation]),
+    "anti-bounce-back sign": (
+        [("g[i] = -gprev[ko] + 2.0 * W[i] * CP * TH;", "g[i] = gprev[ko] + 2.0 * W[i] * CP * TH;")],
+        [test_heated_strip_energy_budget]),
+    "Stefan rows not periodic": (
+        [("if (s->p.problem == ORC_STEFAN) sy = ((sy % ny) + ny) % ny; /* periodic y */", "")],
+        [lambda orc: test_stefan_front_and_profile_match_neumann(orc, 1.0)]),
+    "initial perturbation on [0, 2 amp)": (
+        [("const double delta = p->init_amp * (2.0 * r - 1.0);",
+          "const double delta = p->init_amp * (2.0 * r);")],
+        [test_initial_perturbation_is_uniform_on_plus_minus_amp]),
+    "buoyancy sign": (
+        [("Fy = RHO0 * s->d.gbeta * (T - TM);", "Fy = -RHO0 * s->d.gbeta * (T - TM);")],
+        [test_hot_fluid_rises, test_hydrostatic_balance_sets_force_sign]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_fail_on_planted_mistakes(orc, tmp_path, name):
+    replacements, checks = MUTATIONS[name]
+    path = orc.compile_variant(replacements, str(tmp_path))
+    with orc.variant(path):
+        for check in checks:
+            with pytest.raises(AssertionError):
+                check(orc)
