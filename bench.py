@@ -21,6 +21,13 @@ the same JSON line: each step advances a band of the cavity's rows (same
 width, parameters and per-cell work) sized so that the whole run takes about
 two minutes; the full 1024 rows when K is small.
 
+The default run also serves a seeded Poisson stream of cavity requests
+(mixed grids, Rayleigh numbers and strip positions) with continuous batching
+in BF16 storage with stochastic rounding and, for comparison, one request at a
+time in plain FP32, and reports under "serving" the p50 / p99 time to result,
+the aggregate MLUPS and the 16-bit results' largest melt-fraction and Nusselt
+differences from an FP64 run of the same requests.
+
 --batch N times the batched path instead: N cavities of 256 x 128 (the
 serving size; Ra and strip centre varied, seeded) advanced together, one fused
 launch per step over all of them (graph-replayed); the last step carries the
@@ -147,7 +154,9 @@ def profiled_traffic(precision: str = "fp32", batch: int = 0) -> float | None:
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling around the timed region: a sample
+    just before, one every 100 ms while the block runs (the warm-up and the
+    timed steps), and one just after."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -156,9 +165,23 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.bracket = []
         self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
 
+    def once(self) -> list:
+        """One sample, taken now (the timed region may be too short for the
+        100 ms loop to record any)."""
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                 timeout=10).stdout
+        except (OSError, subprocess.SubprocessError):
+            return []
+        return [[p.strip() for p in line.split(",")] for line in out.splitlines()
+                if len(line.split(",")) >= 9]
+
     def __enter__(self):
+        self.bracket = self.once()
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -177,38 +200,53 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
             self.fh.close()
+        self.bracket += self.once()
 
     def summary(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
-        try:
-            for line in open(self.path):
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        except OSError:
-            pass
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
-        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        if self.proc is not None:
+            try:
+                for line in open(self.path):
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            except OSError:
+                pass
+        inside = len(rows)
+        # the median is over the samples inside the timed region when there are
+        # any, else over the two taken just before and just after it
+        use = rows if rows else self.bracket
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = sorted(float(r[1]) for r in use if r[1].replace(".", "").isdigit())
+        smax = max(float(r[2]) for r in rows + self.bracket if r[2].replace(".", "").isdigit())
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        reasons = sorted({n for r in rows + self.bracket for n, v in zip(names, r[5:9])
+                          if v.lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": inside, "bracket_samples": len(self.bracket),
+                "median_of": "warm-up and timed region" if rows else
+                "samples just before and after the warm-up and timed region"}
 
 
 # ------------------------------------------------------------ CPU oracle arm
 def oracle_mlups(steps: int, warmup: int, threads: int, rows: int = NY) -> tuple[float, float, int]:
-    """Time the FP64 oracle on the same workload (or on its first `rows` rows:
-    the same width, parameters and per-cell work): returns (MLUPS, seconds,
-    steps)."""
+    """Time the FP64 oracle on the same workload, or on a band of `rows` of its
+    rows: the same width, the same derived parameters (nu, alpha, g beta, the
+    rates and the strip, all those of the full 2048 x 1024 cavity) and the same
+    per-cell work.  Returns (MLUPS, seconds, steps)."""
     from oracle import oracle as O
     from paper_1909_13086_gb300 import workloads
 
     nx, ny, p = workloads.cavity_2048x1024()
-    ny = max(2, min(ny, rows))
+    if rows < ny:
+        # The cavity mapping takes its reference length from the height; give
+        # the band the full cavity's alpha directly and the Rayleigh number that
+        # reproduces its g beta over the band's height.
+        d = O.derive(nx, ny, **p)
+        rows = max(2, rows)
+        p = dict(p, alpha_override=d.alpha, Ra=d.gbeta * rows ** 3 / (d.nu * d.alpha))
+        ny = rows
     o = O.Oracle(nx, ny, threads=threads, **p)
     if warmup:
         o.step(warmup)
@@ -330,15 +368,16 @@ def run_ours(args) -> None:
 
     lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream.cuda_stream)
     lbm.lbm_set_diag_every(lat.h, DIAG_EVERY)
-    lat.step(args.warmup)
-    torch.cuda.synchronize()
 
-    # ---- device-resident timing: K sweeps, inputs already in HBM
+    # ---- device-resident timing: K sweeps, inputs already in HBM.  The clock
+    # sampler starts before the warm-up, so that starting nvidia-smi does not
+    # leave the GPU idle just before the timed region.
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
+        lat.step(args.warmup)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         start.record(stream)
         lat.step(args.steps)
         stop.record(stream)
@@ -389,6 +428,8 @@ def run_ours(args) -> None:
         "clocks": clocks.summary(),
         "melt_fraction": d["melt_fraction"],
     }
+    if ws == 1 and not args.no_serving:
+        line["serving"] = serving_leg()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(os.cpu_count() or 1)
     if rank == 0:
@@ -396,6 +437,64 @@ def run_ours(args) -> None:
     lat.close()
     if dist:
         dist.destroy_process_group()
+
+
+# Serving leg of the default run: a seeded Poisson stream of cavity requests
+# (grids 256 x 128 to 2048 x 1024, Ra 1e6 / 1e7 / 1e8, strip centre at five
+# positions) served with continuous batching in 16-bit storage with stochastic
+# rounding, against the same stream served one request at a time in plain FP32.
+SERVING = dict(requests=32, rate_hz=40.0, steps=2000, precision="bf16sr", seed=7, budget_gb=64.0,
+               quantum=100)
+
+
+def serving_leg() -> dict:
+    """p50 / p99 time to result and aggregate MLUPS of both servers, and the
+    accuracy of the batched 16-bit results: every request is also advanced in
+    FP64 on the GPU (batched by grid size), and the largest differences in the
+    final melt fraction and in the mean Nusselt number over the run (from the
+    cumulative heated-wall inflow; the one-step inflow carries the rounding
+    noise of a few hundred wall populations) are reported."""
+    import torch
+
+    from paper_1909_13086_gb300 import lbm, serving
+
+    cfg = SERVING
+    reqs = serving.poisson_stream(cfg["requests"], cfg["rate_hz"], cfg["seed"], cfg["steps"],
+                                  precisions=(cfg["precision"],))
+    res_b, mk_b = serving.serve(reqs, int(cfg["budget_gb"] * 2 ** 30), cfg["quantum"])
+    s = torch.cuda.Stream()
+    res_s, mk_s = serving.sequential_fp32(reqs, s.cuda_stream)
+    batched = serving.summarize(res_b, reqs, mk_b)
+    sequential = serving.summarize(res_s, reqs, mk_s)
+    # FP64 reference of every request, one batch per grid size
+    by_id = {x.rid: x for x in res_b}
+    melt_err, nu_err = 0.0, 0.0
+    for nx, ny in sorted({(r.nx, r.ny) for r in reqs}):
+        group = [r for r in reqs if (r.nx, r.ny) == (nx, ny)]
+        lats = [lbm.Lattice(nx, ny, r.params(), precision="fp64", stream=s.cuda_stream) for r in group]
+        b = lbm.Batch(len(lats), s.cuda_stream)
+        for lat in lats:
+            b.add(lat)
+        b.step(cfg["steps"])
+        for r, lat in zip(group, lats):
+            d64, d16 = lat.diagnostics(), by_id[r.rid].diag
+            melt_err = max(melt_err, abs(d16["melt_fraction"] - d64["melt_fraction"]))
+            # mean Nu over the run is Q_cum times a constant of the request
+            nu_err = max(nu_err, abs(d16["Q_cum"] - d64["Q_cum"]) / abs(d64["Q_cum"]))
+        b.close()
+        for lat in lats:
+            lat.close()
+    return {
+        "stream": f"{cfg['requests']} Poisson requests at {cfg['rate_hz']:g}/s, {cfg['steps']} steps "
+                  "each, grids 256x128 / 512x256 / 1024x512 / 2048x1024, Ra 1e6 / 1e7 / 1e8, strip "
+                  "centre 0.2-0.8 W (seeded)",
+        "batched": {"precision": cfg["precision"], "mode": "continuous batching", **batched},
+        "sequential": {"precision": "fp32", "mode": "one request at a time, FIFO", **sequential},
+        "p99_ratio": sequential["p99_s"] / batched["p99_s"],
+        "mlups_ratio": batched["mlups"] / sequential["mlups"],
+        "melt_err_max_vs_fp64": melt_err,
+        "mean_nu_rel_err_max_vs_fp64": nu_err,
+    }
 
 
 BATCH_NX, BATCH_NY = 256, 128
@@ -420,10 +519,10 @@ def run_batch(args) -> None:
     b = lbm.Batch(n, stream.cuda_stream)
     for lat in lats:
         b.add(lat)
-    b.step(args.warmup)
-    torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clocks:
+        b.step(args.warmup)
+        torch.cuda.synchronize()
         start.record(stream)
         b.step(args.steps)
         stop.record(stream)
@@ -471,6 +570,7 @@ def main(argv=None):
     ap.add_argument("--precision", choices=("fp32", "fp64", "fp16", "bf16", "fp16sr", "bf16sr"), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch", type=int, default=0,
                     help=f"time a batch of this many {BATCH_NX}x{BATCH_NY} cavities instead")
     args = ap.parse_args(argv)

@@ -149,16 +149,37 @@ int lbm_set_diag_every(lbm_handle h, long long k);
 /* Launch shape of the sweep (the tuner's knobs): rows of the lattice walked by
  * each thread of a block (1 to 1024, default 1); the distance, in rows, at
  * which each block asks L2 to prefetch a later block's tile row (0 = off,
- * default 4, or 24 with 16-bit storage); and graph_chunk, the number of
- * sweeps lbm_step captures once into a CUDA graph and then replays (0 =
- * launch every sweep directly; default 128; up to 8 chunk graphs are cached
- * per handle, keyed by buffer parity and the position of the diagnostic
- * sweeps).  When the caller is itself capturing the handle's stream,
- * lbm_step launches directly.  Results do not depend on any of these: the
+ * default 4, or 24 with 16-bit storage); and graph_chunk, the longest piece
+ * of sweeps lbm_step replays from a CUDA graph (0 = launch every sweep
+ * directly; default 128).
+ *
+ * How lbm_step enqueues its n sweeps: it cuts them into pieces that end at
+ * the diagnostic sweeps (every diag_every-th step and the call's last one)
+ * and are at most graph_chunk long.  A piece is identified by its length,
+ * whether it ends with a diagnostic sweep, and the buffer parity it starts
+ * from.  The first time a piece is asked for its sweeps are launched
+ * directly; the second time it is captured into a CUDA graph, which is
+ * replayed from then on (up to 16 pieces are remembered per handle, least
+ * recently used first out).  So repeated calls of one length -- a serving
+ * quantum, a fixed output interval -- run from graphs after the first, and a
+ * one-off call never pays for a capture.  Every sweep, direct or replayed,
+ * is launched with programmatic stream serialization: it is scheduled while
+ * the previous sweep's last blocks drain and waits for that sweep's results
+ * before it reads them.  When the caller is itself capturing the handle's
+ * stream, lbm_step launches directly.  Results do not depend on any of these: the
  * populations never, and the diagnostics of FP32 and 16-bit storage neither
  * (their sums are exact fixed-point integer sums); the FP64 diagnostics sums
  * follow the grouping of cells, to within FP64 rounding.  Errors: LBM_ERR_ARG. */
 int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int graph_chunk);
+
+/* Counters of how the handle's sweeps were enqueued since lbm_create:
+ * launched directly, replayed from captured graphs, and graphs captured. */
+typedef struct {
+    long long sweeps_direct;
+    long long sweeps_replayed;
+    long long graphs_captured;
+} lbm_launch_stats;
+int lbm_get_launch_stats(lbm_handle h, lbm_launch_stats *out);
 
 /* Autotuner: times every launch shape of a small candidate set (rows per block
  * 1, 2, 4; prefetch distance 0, 2, 4, 8, 16, 32 rows) for steps_per_trial
@@ -218,9 +239,13 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
  * of every member lattice form one grid (each block looks up its lattice and
  * tile in a device table), so lattices too small to fill the GPU alone -- the
  * 256 x 128 requests of a serving stream -- share it, and the per-step launch
- * cost is paid once.  The batch replays CUDA graphs of 64-step chunks (captured
- * once per batch composition) and uses its own launch shape (2 rows per block,
- * 4 with 16-bit storage), whatever the members' lbm_set_launch settings.  Each
+ * cost is paid once.  lbm_batch_step cuts its steps into pieces (128 plain
+ * steps while more than 128 remain, then the rest, ending with the diagnostic
+ * step) and, as lbm_step does, replays a piece from a CUDA graph from the
+ * second time it is asked for (graphs are kept per batch composition); every
+ * launch uses programmatic stream serialization.  The batch uses its own
+ * launch shape (2 rows per block, 4 with 16-bit storage), whatever the
+ * members' lbm_set_launch settings.  Each
  * step of a member computes exactly what lbm_step would: the populations are
  * bitwise those of stepping it alone, and so are the diagnostics except on
  * FP64 lattices (summation order, see lbm_set_launch).
@@ -258,11 +283,11 @@ int lbm_batch_step(lbm_batch b, long long n);
 int lbm_batch_destroy(lbm_batch b);
 
 /* One step with no allocation, for callers that cannot allocate device
- * memory at the moment they step -- code running while a stream is being
- * captured into a CUDA graph (where cudaMalloc is not allowed), hosts that
- * hand out device memory only from their own fixed arena, latency-critical
- * loops that must never enter the allocator.  The paper has no counterpart:
- * it is an interface convenience, not part of the method.
+ * memory at the moment they step: hosts that hand out device memory only from
+ * a fixed arena of their own, plug-ins that must not touch the host program's
+ * allocator, latency-critical loops that must never enter an allocator.  The
+ * paper has no counterpart: it is an interface convenience, not part of the
+ * method.
  *
  * Advances the lattice held in the caller's device buffer `src` by one fused
  * sweep with diagnostics (the same kernel and arithmetic as lbm_step) into the
@@ -281,7 +306,11 @@ int lbm_batch_destroy(lbm_batch b);
  * lattice: ceil(nx / 128) * ny <= 65536 (e.g. 4096 x 2048); larger ones get
  * LBM_ERR_ARG -- use lbm_create / lbm_step.  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares
+ * current and keeps it for later calls; make that first call before any
+ * stream capture.  The kept address belongs to the device's context as it was
+ * then: after cudaDeviceReset (or any teardown of the primary context) it is
+ * stale, so do not call lbm_step_static on a device after resetting it.  With
+ * out non-NULL the call also synchronises the stream.  Every call shares
  * the one array, clearing what must start at zero: calls whose work overlaps
  * on the GPU (other streams, other host threads) race and must be serialised
  * by the caller.  Allocates nothing and calls no allocating routine.  Errors

@@ -38,15 +38,19 @@ constexpr int kDefaultPrefetch = 4;  // L2 prefetch distance in rows (tuned on G
 // the L2 prefetch pays further ahead (2048 x 1024 cavity on GB300: 8 rows
 // 38.6 us, 24 rows 38.3 us FP16-SR; 8 rows 35.1 us, 24 rows 33.6 us FP16).
 constexpr int kDefaultPrefetch16 = 24;
-constexpr int kDefaultGraphChunk = 128;  // steps per replayed CUDA graph (0 = direct launches)
-constexpr int kGraphCache = 8;           // cached chunk graphs per handle
+constexpr int kDefaultGraphChunk = 128;  // longest graph-replayed piece (0 = direct launches)
+constexpr int kGraphCache = 16;          // cached piece graphs per handle
 
-// One captured chunk of sweeps: valid for the buffer parity and the position
-// of the diagnostic sweeps (step mod diag_every) it was captured with.
+// A piece of a step sequence: len sweeps from a given buffer parity, the last
+// one diagnostic or not (every other sweep of a piece is plain).  Its graph is
+// captured the second time the piece is asked for -- a one-off call never
+// pays for a capture -- and replayed from then on.  exec == nullptr: seen
+// once, not captured yet.
 struct ChunkGraph {
     bool used = false;
     int parity = 0;
-    long long key = 0;
+    int len = 0;
+    bool diag = false;
     cudaGraphExec_t exec = nullptr;
     unsigned long long stamp = 0;
 };
@@ -62,6 +66,7 @@ struct lbm_s {
     int graph_chunk = kDefaultGraphChunk;
     ChunkGraph graphs[kGraphCache];
     unsigned long long graph_clock = 0;
+    lbm_launch_stats stats{};   // sweeps launched directly / replayed, graphs captured
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *buf[2] = {nullptr, nullptr};  // 18 planes each
@@ -257,14 +262,15 @@ int derive(lbm_s *h, const lbm_params *p, lbm_derived *d) {
 }
 
 // One sweep (plus the diagnostics fold after a diagnostic sweep), enqueued on
-// the stream; advances the host's view of the state.
+// the stream with programmatic serialization; advances the host's view of
+// the state.
 template <typename real, typename S>
 int launch_one(lbm_s *h, bool diag) {
     const long long next = h->step + 1;
     SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
     a.step = next;
     cudaError_t e = launch_lattice<real, S>(a, h->p.problem, h->p.flow_on != 0, diag ? kSweepDiag : kSweep,
-                                         h->grid, h->block, h->stream);
+                                         h->grid, h->block, h->stream, true);
     if (e != cudaSuccess) return set_err(h, LBM_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(e));
     h->cur ^= 1;
     h->has_prev = true;
@@ -276,85 +282,102 @@ bool diag_step(const lbm_s *h, long long step) { return h->diag_every > 0 && ste
 
 void drop_graphs(lbm_s *h) {
     for (ChunkGraph &g : h->graphs) {
-        if (g.used && g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.exec) cudaGraphExecDestroy(g.exec);
         g = ChunkGraph();
     }
 }
 
-// Replays (capturing first if needed) a graph of graph_chunk sweeps.  Kernel
-// arguments are fixed per chunk: the ping-pong pointers depend only on the
-// parity of the starting buffer and the diagnostic sweeps only on the
-// starting step mod diag_every; everything that changes from step to step
-// (step counter, heated-wall sums, tickets) lives in device memory.
-// Returns LBM_OK, or 1 if graphs cannot be used here (caller launches directly).
+// Enqueues one piece: len sweeps, the last one diagnostic if diag.  Kernel
+// arguments are fixed per piece -- the ping-pong pointers depend only on the
+// starting parity -- and everything that changes from step to step (step
+// counter, heated-wall sums, tickets, rounding seeds) lives in device memory,
+// so a captured piece replays correctly at any later step.
 template <typename real, typename S>
-int replay_chunk(lbm_s *h) {
-    const int G = h->graph_chunk;
-    const long long key = h->diag_every > 0 ? h->step % h->diag_every : -1;
-    ChunkGraph *slot = nullptr;
-    for (ChunkGraph &g : h->graphs)
-        if (g.used && g.parity == h->cur && g.key == key) slot = &g;
-    if (!slot) {
+int run_piece(lbm_s *h, long long len, bool diag) {
+    bool graphs = h->graph_chunk >= 2 && len >= 2 && len <= h->graph_chunk;
+    if (graphs) {
         cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(h->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone)
-            return 1;  // the caller is capturing this stream itself
-        ChunkGraph *victim = &h->graphs[0];
-        for (ChunkGraph &g : h->graphs) {
-            if (!g.used) { victim = &g; break; }
-            if (g.stamp < victim->stamp) victim = &g;
-        }
-        if (victim->used && victim->exec) cudaGraphExecDestroy(victim->exec);
-        *victim = ChunkGraph();
-        const int cur0 = h->cur;
-        const long long step0 = h->step;
-        const bool prev0 = h->has_prev;
-        CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        int rc = LBM_OK;
-        for (int j = 0; j < G && rc == LBM_OK; ++j) rc = launch_one<real, S>(h, diag_step(h, h->step + 1));
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-        h->cur = cur0;
-        h->step = step0;
-        h->has_prev = prev0;
-        if (rc != LBM_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (e != cudaSuccess)
-            return set_err(h, LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess)
-            return set_err(h, LBM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
-        victim->used = true;
-        victim->parity = cur0;
-        victim->key = key;
-        victim->exec = exec;
-        slot = victim;
+        graphs = cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st == cudaStreamCaptureStatusNone;
     }
-    slot->stamp = ++h->graph_clock;
-    CUDA_TRY(h, cudaGraphLaunch(slot->exec, h->stream));
-    h->cur ^= (G & 1);
-    h->has_prev = true;
-    h->step += G;
+    ChunkGraph *slot = nullptr;
+    if (graphs) {
+        for (ChunkGraph &g : h->graphs)
+            if (g.used && g.parity == h->cur && g.len == len && g.diag == diag) slot = &g;
+        if (!slot) {  // first sighting: remember it, launch directly
+            ChunkGraph *victim = &h->graphs[0];
+            for (ChunkGraph &g : h->graphs) {
+                if (!g.used) { victim = &g; break; }
+                if (g.stamp < victim->stamp) victim = &g;
+            }
+            if (victim->exec) cudaGraphExecDestroy(victim->exec);
+            *victim = ChunkGraph();
+            victim->used = true;
+            victim->parity = h->cur;
+            victim->len = (int)len;
+            victim->diag = diag;
+            victim->stamp = ++h->graph_clock;
+            graphs = false;
+        } else if (!slot->exec) {  // second sighting: capture it
+            const int cur0 = h->cur;
+            const long long step0 = h->step;
+            const bool prev0 = h->has_prev;
+            CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = LBM_OK;
+            for (long long j = 0; j < len && rc == LBM_OK; ++j) rc = launch_one<real, S>(h, diag && j == len - 1);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+            h->cur = cur0;
+            h->step = step0;
+            h->has_prev = prev0;
+            if (rc != LBM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess)
+                return set_err(h, LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess)
+                return set_err(h, LBM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+            slot->exec = exec;
+            h->stats.graphs_captured += 1;
+        }
+    }
+    if (graphs) {
+        slot->stamp = ++h->graph_clock;
+        CUDA_TRY(h, cudaGraphLaunch(slot->exec, h->stream));
+        h->cur ^= (int)(len & 1);
+        h->has_prev = true;
+        h->step += len;
+        h->stats.sweeps_replayed += len;
+        return LBM_OK;
+    }
+    for (long long j = 0; j < len; ++j) {
+        const int rc = launch_one<real, S>(h, diag && j == len - 1);
+        if (rc != LBM_OK) return rc;
+    }
+    h->stats.sweeps_direct += len;
     return LBM_OK;
 }
 
+// n sweeps, cut into pieces that end at the diagnostic sweeps (every
+// diag_every-th step and the call's last one) and are at most graph_chunk
+// long: with diag_every = 100 every full piece is the same 100-sweep graph.
 template <typename real, typename S>
 int enqueue_steps(lbm_s *h, long long n) {
-    long long left = n;
-    // whole chunks by graph replay; the last sweep (always diagnostic) and the
-    // remainder by direct launches
-    while (h->graph_chunk >= 2 && left > h->graph_chunk) {
-        const int rc = replay_chunk<real, S>(h);
-        if (rc == 1) break;
+    long long done = 0;
+    while (done < n) {
+        long long to_diag = n - done;  // sweeps up to and including the next diagnostic one
+        if (h->diag_every > 0) {
+            const long long k = h->diag_every - h->step % h->diag_every;
+            if (k < to_diag) to_diag = k;
+        }
+        const bool full = h->graph_chunk >= 2 && to_diag > h->graph_chunk;
+        const long long len = full ? h->graph_chunk : to_diag;
+        const int rc = run_piece<real, S>(h, len, !full);
         if (rc != LBM_OK) return rc;
-        left -= h->graph_chunk;
-    }
-    for (; left > 0; --left) {
-        const int rc = launch_one<real, S>(h, left == 1 || diag_step(h, h->step + 1));
-        if (rc != LBM_OK) return rc;
+        done += len;
     }
     return LBM_OK;
 }
@@ -384,7 +407,7 @@ int enqueue_fields(lbm_s *h, double *out[6]) {
         SweepArgs<real> a = make_args<real>(h, h->buf[h->cur ^ 1], nullptr);
         a.oH = out[0]; a.oT = out[1]; a.oFL = out[2]; a.oUX = out[3]; a.oUY = out[4]; a.oRHO = out[5];
         e = launch_lattice<real, S>(a, h->p.problem, h->p.flow_on != 0, kFields, h->grid, h->block,
-                                 h->stream);
+                                 h->stream, false);
     }
     if (e != cudaSuccess)
         return set_err(h, LBM_ERR_CUDA, "fields launch failed: %s", cudaGetErrorString(e));
@@ -545,6 +568,12 @@ int lbm_step(lbm_handle h, long long n) {
     if (n == 0) return LBM_OK;
     DeviceGuard g(h->device);
     return by_precision(h->precision, [&](auto t) { return BTRIRT_T(t, enqueue_steps)(h, n); });
+}
+
+int lbm_get_launch_stats(lbm_handle h, lbm_launch_stats *out) {
+    if (!h || !out) return set_err(h, LBM_ERR_ARG, "NULL argument");
+    *out = h->stats;
+    return LBM_OK;
 }
 
 int lbm_set_diag_every(lbm_handle h, long long k) {
@@ -842,8 +871,11 @@ struct lbm_batch_s {
     int uniform = 0;          // blocks per member when all members have the same count
     bool dirty = true;        // table must be rebuilt and uploaded
     int precision = -1, problem = -1, flow = -1;
-    int graph_chunk = 64;     // even: parities return to their start value
-    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 128;    // longest graph-replayed piece; even, so that every
+                              // piece starts at an even step of the call
+    ChunkGraph graphs[kGraphCache];  // pieces as for a single lattice (parity unused:
+                                     // the members' parities are a device table)
+    unsigned long long graph_clock = 0;
     cudaEvent_t ev = nullptr;
     lbm_alloc_fn alloc = nullptr;
     lbm_free_fn release = nullptr;
@@ -872,8 +904,10 @@ void batch_free(lbm_batch_s *b, void *p) {
 }
 
 void batch_drop_graph(lbm_batch_s *b) {
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
+    for (ChunkGraph &g : b->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = ChunkGraph();
+    }
 }
 
 template <typename real>
@@ -934,40 +968,74 @@ int batch_steps(lbm_batch_s *b, long long n) {
     for (int r = 0; r < nm; ++r) b->host_parity[r] = b->members[r]->cur;
     BATCH_TRY(cudaMemcpyAsync(b->parity, b->host_parity.data(), nm * sizeof(int), cudaMemcpyHostToDevice,
                               b->stream));
+    // Pieces: graph_chunk plain sweeps while more than that remain, then the
+    // rest, ending with the diagnostic sweep.  Step j of a piece uses buffer
+    // parity parity[r] ^ (j & 1); pieces start at even steps of the call, so
+    // a captured piece replays anywhere.  As for a single lattice, a piece's
+    // graph is captured the second time it is asked for.
     long long done = 0;
     const int K = b->graph_chunk;
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     BATCH_TRY(cudaStreamIsCapturing(b->stream, &st));
-    const bool graphs = K >= 2 && st == cudaStreamCaptureStatusNone;
-    while (graphs && n - done > K) {
-        if (!b->graph) {
-            BATCH_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = cudaSuccess;
-            for (int j = 0; j < K && e == cudaSuccess; ++j)
-                e = launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->uniform, b->nblocks,
-                                          b->problem, b->flow != 0, false, j, b->stream);
-            cudaGraph_t g = nullptr;
-            const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-            if (e != cudaSuccess || e2 != cudaSuccess) {
-                if (g) cudaGraphDestroy(g);
-                return batch_err(LBM_ERR_CUDA, "batch graph capture failed: %s",
-                                 cudaGetErrorString(e != cudaSuccess ? e : e2));
-            }
-            const cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e3 != cudaSuccess) {
-                b->graph = nullptr;
-                return batch_err(LBM_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e3));
+    const bool capturing = st != cudaStreamCaptureStatusNone;
+    auto direct = [&](long long from, long long len, bool diag) -> int {
+        for (long long j = 0; j < len; ++j) {
+            const cudaError_t e = launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->uniform,
+                                                        b->nblocks, b->problem, b->flow != 0,
+                                                        diag && j == len - 1, (int)((from + j) & 1),
+                                                        b->stream, true);
+            if (e != cudaSuccess) return batch_err(LBM_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+        }
+        return LBM_OK;
+    };
+    while (done < n) {
+        const bool full = K >= 2 && n - done > K;
+        const long long len = full ? K : n - done;
+        const bool diag = !full;
+        ChunkGraph *slot = nullptr;
+        const bool graphs = K >= 2 && len >= 2 && len <= K && !capturing;
+        if (graphs) {
+            for (ChunkGraph &g : b->graphs)
+                if (g.used && g.len == len && g.diag == diag) slot = &g;
+            if (!slot) {
+                ChunkGraph *victim = &b->graphs[0];
+                for (ChunkGraph &g : b->graphs) {
+                    if (!g.used) { victim = &g; break; }
+                    if (g.stamp < victim->stamp) victim = &g;
+                }
+                if (victim->exec) cudaGraphExecDestroy(victim->exec);
+                *victim = ChunkGraph();
+                victim->used = true;
+                victim->len = (int)len;
+                victim->diag = diag;
+                victim->stamp = ++b->graph_clock;
+            } else if (!slot->exec) {
+                BATCH_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                const int rc = direct(0, len, diag);
+                cudaGraph_t g = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                if (rc != LBM_OK || e2 != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc != LBM_OK ? rc
+                                        : batch_err(LBM_ERR_CUDA, "batch graph capture failed: %s",
+                                                    cudaGetErrorString(e2));
+                }
+                const cudaError_t e3 = cudaGraphInstantiate(&slot->exec, g, 0);
+                cudaGraphDestroy(g);
+                if (e3 != cudaSuccess) {
+                    slot->exec = nullptr;
+                    return batch_err(LBM_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e3));
+                }
             }
         }
-        BATCH_TRY(cudaGraphLaunch(b->graph, b->stream));
-        done += K;
-    }
-    for (; done < n; ++done) {
-        const cudaError_t e =
-            launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->uniform, b->nblocks, b->problem,
-                                  b->flow != 0, done == n - 1, (int)(done & 1), b->stream);
-        if (e != cudaSuccess) return batch_err(LBM_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+        if (slot && slot->exec) {
+            slot->stamp = ++b->graph_clock;
+            BATCH_TRY(cudaGraphLaunch(slot->exec, b->stream));
+        } else {
+            const int rc = direct(done, len, diag);
+            if (rc != LBM_OK) return rc;
+        }
+        done += len;
     }
     for (lbm_s *h : b->members) {
         h->step += n;
@@ -1213,12 +1281,12 @@ extern "C" int lbm_step_static(const void *src, void *dst, int nx, int ny, int p
         SweepArgs<double> a = make_args<double>(&t, src, dst);
         a.step = step + 1;
         e = launch_lattice<double, double>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block,
-                                           t.stream);
+                                           t.stream, false);
     } else {
         SweepArgs<float> a = make_args<float>(&t, src, dst);
         a.step = step + 1;
         e = launch_lattice<float, float>(a, p->problem, p->flow_on != 0, kSweepDiag, t.grid, t.block,
-                                         t.stream);
+                                         t.stream, false);
     }
     if (e != cudaSuccess)
         return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: launch failed: %s", cudaGetErrorString(e));

@@ -95,9 +95,12 @@ template <bool SR>
 struct F16;
 template <bool SR>
 struct BF16;
+// pdl: launch the sweep with programmatic stream serialization, so that it
+// is scheduled while the previous kernel of the stream drains (the kernel
+// waits for that kernel's completion before it touches memory).
 template <typename real, typename S>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
-                           dim3 grid, dim3 block, cudaStream_t s);
+                           dim3 grid, dim3 block, cudaStream_t s, bool pdl);
 template <typename real, typename S>
 cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim3 grid,
                         dim3 block, cudaStream_t s);
@@ -123,7 +126,7 @@ struct BatchEntry {
 template <typename real, typename S>
 cudaError_t launch_batch(const void *entries, const int *starts, const int *parity, int n,
                          int uniform, int nblocks, int problem, bool flow, bool diag, int j,
-                         cudaStream_t s);
+                         cudaStream_t s, bool pdl);
 // Tile-major buffer <-> plane-major FP64 staging (18 planes of nx*ny, f then g).
 // to_staging = true packs buf into stage; false unpacks stage into buf (and,
 // if buf2 is non-NULL, the f planes into buf2 as well).  Values in the staging

@@ -35,6 +35,7 @@
 #include <stdint.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "lbm_internal.h"
 
@@ -473,6 +474,18 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
     }
 }
 
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel
+// launched with the programmatic-serialization attribute may start while the
+// previous kernel of its stream is still running: each block first lets the
+// next kernel be scheduled (that happens once every block of this grid has
+// done so, i.e. when the last wave is resident), then waits until the previous
+// kernel has completed and its memory is visible before it reads or writes
+// anything.  Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- reductions ----
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -559,17 +572,33 @@ __device__ __forceinline__ void diag_partial(typename DiagAcc<real>::T sfl,
     }
 }
 
-// Fold of the per-block partials in two levels: block r of the fold kernel
-// folds partials [r T, (r + 1) T) (one load per thread, fixed tree) into a
-// level-2 partial; the last of those blocks to take a ticket folds the level-2
-// partials and writes the record.  The order is fixed, so the record is
-// bitwise reproducible (and on the FP32 path exact in fixed point).
+// Fold of the per-block partials in two levels: thread t of fold block r
+// folds partials r T + t, r T + t + G T, ... (G fold blocks, T threads each;
+// a fixed order), then the block folds its threads' values (fixed tree) into
+// a level-2 partial; the last of the G blocks to take a ticket folds the
+// level-2 partials the same way and writes the record.  The order is fixed,
+// so the record is bitwise reproducible (and on the FP32 path exact in fixed
+// point).  G is at most T, so the second level is one pass of one block.
 constexpr int kReduceThreads = 1024;
 
 template <typename A>
 __device__ __forceinline__ void load4(A (&acc)[4], const A *part, unsigned idx, bool ok) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[k] = ok ? __ldcg(part + 4 * (size_t)idx + k) : A(0);
+}
+
+// acc (kinds {sum, sum, max, max}) folded with partials first, first + step, ...
+// below n.
+template <typename A>
+__device__ __forceinline__ void fold4_strided(A (&acc)[4], const A *part, size_t first, size_t step,
+                                              size_t n) {
+    for (size_t i = first; i < n; i += step) {
+        const A *q = part + 4 * i;
+        acc[0] += __ldcg(q + 0);
+        acc[1] += __ldcg(q + 1);
+        acc[2] = max(acc[2], __ldcg(q + 2));
+        acc[3] = max(acc[3], __ldcg(q + 3));
+    }
 }
 
 // A full history entry at a diagnostic step: step, this step's heated-wall
@@ -590,9 +619,11 @@ __global__ void __launch_bounds__(kReduceThreads)
     __shared__ double sh[32 * 4];
     __shared__ bool last;
     const int kind[4] = {0, 0, 1, 1};
-    A acc[4];
-    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-    load4(acc, reinterpret_cast<const A *>(dpart), idx, idx < nblk);
+    pdl_launch_dependents();
+    pdl_wait();  // the sweep's partials
+    A acc[4] = {A(0), A(0), A(0), A(0)};
+    fold4_strided(acc, reinterpret_cast<const A *>(dpart), (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+                  (size_t)gridDim.x * blockDim.x, nblk);
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
     block_fold<4, A>(acc, kind, sh);
@@ -606,7 +637,7 @@ __global__ void __launch_bounds__(kReduceThreads)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    load4(acc, reinterpret_cast<const A *>(part2), threadIdx.x, threadIdx.x < gridDim.x);
+    load4(acc, reinterpret_cast<const A *>(part2), threadIdx.x, threadIdx.x < gridDim.x);  // G <= T
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
     block_fold<4, A>(acc, kind, sh);
@@ -784,6 +815,8 @@ template <typename real, typename S, int PROB, bool FLOW, int MODE>
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     lattice_kernel(const SweepArgs<real> a) {
     __shared__ double sh[32 * 4];
+    pdl_launch_dependents();
+    pdl_wait();  // the previous sweep's populations, tickets and record
     sweep_block<real, S, PROB, FLOW, MODE>(a, blockIdx.x, blockIdx.y, gridDim.x, sh);
 }
 
@@ -815,6 +848,11 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     __shared__ double sh[32 * 4];
     __shared__ __align__(16) unsigned char entry_sh[sizeof(BatchEntry<real>)];
     __shared__ int meta[2];
+    pdl_launch_dependents();
+    // The table and the parity words are written only by copies the host
+    // orders before the batch's launches, never by a kernel: the block reads
+    // its entry while the previous step may still be running, and waits for
+    // that step only before touching the populations.
     int r;
     if (uniform > 0) {
         r = (int)(blockIdx.x / (unsigned)uniform);
@@ -829,6 +867,7 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
         d4[k] = __ldg(s4 + k);
     if (threadIdx.x == 0) meta[1] = __ldg(parity + r) ^ (j & 1);
     __syncthreads();
+    pdl_wait();
     const BatchEntry<real> &e = *reinterpret_cast<const BatchEntry<real> *>(entry_sh);
     const int l = blockIdx.x - e.start;
     sweep_block<real, S, PROB, FLOW, MODE>(e.a[meta[1]], l % e.gx, l / e.gx, e.gx, sh);
@@ -842,6 +881,8 @@ __global__ void __launch_bounds__(kReduceThreads)
     batch_diag_reduce_kernel(const BatchEntry<real> *entries) {
     __shared__ double sh[32 * 4];
     const int kind[4] = {0, 0, 1, 1};
+    pdl_launch_dependents();
+    pdl_wait();  // the batch step's partials
     const BatchEntry<real> &e = entries[blockIdx.x];
     const SweepArgs<real> &a = e.a[0];
     const unsigned nblk = (unsigned)e.gx * (unsigned)e.gy;
@@ -983,68 +1024,83 @@ __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, in
 }
 
 // ---- launch dispatch (instantiated per storage type in sweep_*.cu) ----
+// A launch, with the programmatic-serialization attribute when pdl is set.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                            bool pdl, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename real, typename S, int PROB, bool FLOW>
 static cudaError_t launch_mode(const SweepArgs<real> &a, int mode, dim3 grid, dim3 block,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool pdl) {
     switch (mode) {
-        case kSweep: lattice_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(a); break;
+        case kSweep: return launch_k(lattice_kernel<real, S, PROB, FLOW, kSweep>, grid, block, s, pdl, a);
         case kSweepDiag:
-            lattice_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(a);
-            break;
+            return launch_k(lattice_kernel<real, S, PROB, FLOW, kSweepDiag>, grid, block, s, pdl, a);
         case kFields: lattice_kernel<real, S, PROB, FLOW, kFields><<<grid, block, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+// The fold after a diagnostic sweep (or the init kernel); pdl as for the sweep.
 template <typename real>
-static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, bool init, cudaStream_t s) {
+static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, bool init, cudaStream_t s,
+                                      bool pdl) {
     const unsigned nblk = grid.x * grid.y;
-    const unsigned nred = (nblk + kReduceThreads - 1) / kReduceThreads;  // <= kReduceThreads
-    diag_reduce_kernel<typename DiagAcc<real>::T><<<nred, kReduceThreads, 0, s>>>(
-        a.dpart, nblk, a.dpart2, a.dticket, a.rec, init ? 1 : 0, a.hist, a.hist_cap,
-        (double)a.nx * (double)a.ny);
-    return cudaGetLastError();
+    unsigned nred = (nblk + kReduceThreads - 1) / kReduceThreads;
+    if (nred > (unsigned)kReduceThreads) nred = kReduceThreads;  // level 2 is one block's pass
+    return launch_k(diag_reduce_kernel<typename DiagAcc<real>::T>, dim3(nred), dim3(kReduceThreads), s,
+                    pdl, (const double *)a.dpart, nblk, a.dpart2, a.dticket, a.rec, init ? 1 : 0,
+                    a.hist, a.hist_cap, (double)a.nx * (double)a.ny);
 }
 
 template <typename real, typename S>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
-                           dim3 grid, dim3 block, cudaStream_t s) {
+                           dim3 grid, dim3 block, cudaStream_t s, bool pdl) {
     cudaError_t e;
     if (problem == kCavity)
-        e = flow ? launch_mode<real, S, kCavity, true>(a, mode, grid, block, s)
-                 : launch_mode<real, S, kCavity, false>(a, mode, grid, block, s);
+        e = flow ? launch_mode<real, S, kCavity, true>(a, mode, grid, block, s, pdl)
+                 : launch_mode<real, S, kCavity, false>(a, mode, grid, block, s, pdl);
     else
-        e = flow ? launch_mode<real, S, kStefan, true>(a, mode, grid, block, s)
-                 : launch_mode<real, S, kStefan, false>(a, mode, grid, block, s);
-    if (e == cudaSuccess && mode == kSweepDiag) e = launch_diag_reduce(a, grid, false, s);
+        e = flow ? launch_mode<real, S, kStefan, true>(a, mode, grid, block, s, pdl)
+                 : launch_mode<real, S, kStefan, false>(a, mode, grid, block, s, pdl);
+    if (e == cudaSuccess && mode == kSweepDiag) e = launch_diag_reduce(a, grid, false, s, pdl);
     return e;
 }
 
 template <typename real, typename S>
 cudaError_t launch_batch(const void *entries, const int *starts, const int *parity, int n,
                          int uniform, int nblocks, int problem, bool flow, bool diag, int j,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool pdl) {
     const BatchEntry<real> *e = static_cast<const BatchEntry<real> *>(entries);
     const dim3 grid(nblocks), block(kTW);
-#define BTRIRT_BATCH(PROB, FLOW)                                                                 \
-    if (diag)                                                                                    \
-        batch_kernel<real, S, PROB, FLOW, kSweepDiag><<<grid, block, 0, s>>>(e, starts, parity,  \
-                                                                             n, uniform, j);     \
-    else                                                                                         \
-        batch_kernel<real, S, PROB, FLOW, kSweep><<<grid, block, 0, s>>>(e, starts, parity, n,   \
-                                                                         uniform, j);
+    cudaError_t err;
+#define BTRIRT_BATCH(PROB, FLOW)                                                                   \
+    err = diag ? launch_k(batch_kernel<real, S, PROB, FLOW, kSweepDiag>, grid, block, s, pdl, e,   \
+                          starts, parity, n, uniform, j)                                           \
+               : launch_k(batch_kernel<real, S, PROB, FLOW, kSweep>, grid, block, s, pdl, e, starts, \
+                          parity, n, uniform, j);
     if (problem == kCavity) {
         if (flow) { BTRIRT_BATCH(kCavity, true) } else { BTRIRT_BATCH(kCavity, false) }
     } else {
         if (flow) { BTRIRT_BATCH(kStefan, true) } else { BTRIRT_BATCH(kStefan, false) }
     }
 #undef BTRIRT_BATCH
-    cudaError_t err = cudaGetLastError();
-    if (err == cudaSuccess && diag) {
-        batch_diag_reduce_kernel<real, typename DiagAcc<real>::T><<<n, kReduceThreads, 0, s>>>(e);
-        err = cudaGetLastError();
-    }
+    if (err == cudaSuccess && diag)
+        err = launch_k(batch_diag_reduce_kernel<real, typename DiagAcc<real>::T>, dim3(n),
+                       dim3(kReduceThreads), s, pdl, e);
     return err;
 }
 
@@ -1053,7 +1109,7 @@ cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim
                         dim3 block, cudaStream_t s) {
     init_kernel<real, S><<<grid, block, 0, s>>>(a, amp, seed);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_diag_reduce(a, grid, true, s);
+    if (e == cudaSuccess) e = launch_diag_reduce(a, grid, true, s, false);
     return e;
 }
 
@@ -1078,13 +1134,13 @@ cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, 
 // Explicit instantiation of every launcher for one (compute, storage) pair.
 #define BTRIRT_INSTANTIATE(REAL, S)                                                             \
     template cudaError_t launch_lattice<REAL, S>(const SweepArgs<REAL> &, int, bool, int, dim3,  \
-                                                 dim3, cudaStream_t);                            \
+                                                 dim3, cudaStream_t, bool);                      \
     template cudaError_t launch_init<REAL, S>(const SweepArgs<REAL> &, double, uint64_t, dim3,   \
                                               dim3, cudaStream_t);                               \
     template cudaError_t launch_fields0<REAL, S>(const SweepArgs<REAL> &, bool, dim3, dim3,      \
                                                  cudaStream_t);                                  \
     template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t); \
     template cudaError_t launch_batch<REAL, S>(const void *, const int *, const int *, int, int,  \
-                                               int, int, bool, bool, int, cudaStream_t);
+                                               int, int, bool, bool, int, cudaStream_t, bool);
 
 }  // namespace btrirt

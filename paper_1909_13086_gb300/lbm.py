@@ -62,8 +62,13 @@ class lbm_diag(ctypes.Structure):
         ("nan_flag", ctypes.c_int)]
 
 
+class lbm_launch_stats(ctypes.Structure):
+    _fields_ = [("sweeps_direct", ctypes.c_longlong), ("sweeps_replayed", ctypes.c_longlong),
+                ("graphs_captured", ctypes.c_longlong)]
+
+
 EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_set_diag_every",
-            "lbm_set_launch",
+            "lbm_set_launch", "lbm_get_launch_stats",
             "lbm_read_fields", "lbm_diagnostics", "lbm_read_populations", "lbm_write_populations",
             "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
@@ -92,6 +97,7 @@ def lib() -> ctypes.CDLL:
     L.lbm_step.argtypes = [H, ctypes.c_longlong]
     L.lbm_set_diag_every.argtypes = [H, ctypes.c_longlong]
     L.lbm_set_launch.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.lbm_get_launch_stats.argtypes = [H, ctypes.POINTER(lbm_launch_stats)]
     L.lbm_read_fields.argtypes = [H, ctypes.c_uint] + [_D] * 6
     L.lbm_diagnostics.argtypes = [H, ctypes.POINTER(lbm_diag)]
     L.lbm_read_populations.argtypes = [H, _D, _D, ctypes.POINTER(ctypes.c_longlong)]
@@ -174,6 +180,12 @@ def lbm_set_diag_every(h, k: int) -> None:
 
 def lbm_set_launch(h, rows: int = 1, prefetch: int = 4, graph_chunk: int = 128) -> None:
     _check(lib().lbm_set_launch(h, int(rows), int(prefetch), int(graph_chunk)), h)
+
+
+def lbm_get_launch_stats(h) -> dict:
+    st = lbm_launch_stats()
+    _check(lib().lbm_get_launch_stats(h, ctypes.byref(st)), h)
+    return {n: getattr(st, n) for n, _ in lbm_launch_stats._fields_}
 
 
 def lbm_read_fields(h, mask: int, H=None, T=None, fl=None, ux=None, uy=None, rho=None) -> None:

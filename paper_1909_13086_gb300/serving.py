@@ -65,6 +65,7 @@ class Result:
     finish: float
     ok: bool
     diag: dict
+    fields: dict | None = None   # the final H, T, f_l, u fields (keep_fields=True)
 
     @property
     def latency(self) -> float:
@@ -143,8 +144,10 @@ class Server:
     CLASS_CAP = {0: 1 << 30, 1: 8, 2: 2, 3: 1}
 
     def __init__(self, hbm_budget_bytes: int, quantum: int = 100, max_batch: int = 256,
-                 autotune: bool = False, class_cap: dict | None = None, policy: str = "equal"):
+                 autotune: bool = False, class_cap: dict | None = None, policy: str = "equal",
+                 keep_fields: bool = False):
         self.class_cap = dict(self.CLASS_CAP if class_cap is None else class_cap)
+        self.keep_fields = keep_fields
         self.policy = policy
         self.budget = int(hbm_budget_bytes)
         self.quantum = int(quantum)
@@ -213,7 +216,8 @@ class Server:
                 r, lat, start = g.members.pop(rid)
                 del g.remaining[rid]
                 d = lat.diagnostics(raise_on_diverged=False)
-                done.append(Result(rid, r.arrival, start, now_fn(), d["nan_flag"] == 0, d))
+                fields = lat.fields(("H", "T", "fl", "ux", "uy")) if self.keep_fields else None
+                done.append(Result(rid, r.arrival, start, now_fn(), d["nan_flag"] == 0, d, fields))
                 g.batch.remove(lat)
                 lat.close()
                 self.used -= footprint_bytes(r.nx, r.ny, r.precision)
@@ -230,15 +234,16 @@ class Server:
 
 def serve(requests, hbm_budget_bytes: int, quantum: int = 100, autotune: bool = False,
           clock=time.perf_counter, max_batch: int = 256, class_cap: dict | None = None,
-          policy: str = "equal"):
+          policy: str = "equal", keep_fields: bool = False):
     """Serve a request stream with continuous batching; arrivals are replayed
-    in real time relative to the start.  Returns (results, makespan_s)."""
+    in real time relative to the start.  Returns (results, makespan_s).
+    keep_fields: each result also carries its lattice's final fields."""
     pending = sorted(requests, key=lambda r: r.arrival)
     # Lattices come and go while other groups run: take their memory from the
     # caching allocator, since cudaFree would wait for the whole device.
     lbm.use_torch_allocator()
     srv = Server(hbm_budget_bytes, quantum, max_batch=max_batch, autotune=autotune,
-                 class_cap=class_cap, policy=policy)
+                 class_cap=class_cap, policy=policy, keep_fields=keep_fields)
     t0 = clock()
     now = lambda: clock() - t0  # noqa: E731
     results: list[Result] = []

@@ -113,6 +113,23 @@ def test_clock_summary_parses_nvidia_smi_csv(tmp_path):
     s = cs.summary()
     assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
     assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+    assert s["median_of"] == "warm-up and timed region"
+
+
+def test_clock_summary_of_a_short_region_uses_the_bracket(tmp_path):
+    """A timed region shorter than the 100 ms sampling period leaves the loop
+    with no sample: the samples taken just before and after it still give a
+    clock and the throttle reasons."""
+    cs = bench.ClockSampler(0)
+    cs.path = str(tmp_path / "c.csv")
+    cs.proc = object()
+    open(cs.path, "w").close()
+    row = "0, 1965, 2070, 700.0, 0x0, Not Active, Not Active, Active, Not Active"
+    cs.bracket = [[p.strip() for p in row.split(",")], [p.strip() for p in row.split(",")]]
+    s = cs.summary()
+    assert s["sm_mhz"] == 1965.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 0
+    assert s["reasons"] == ["sw_thermal_slowdown"] and s["bracket_samples"] == 2
+    assert s["median_of"].startswith("samples just before")
 
 
 def test_reference_arm_line(capsys, monkeypatch):

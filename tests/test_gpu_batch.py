@@ -1,6 +1,7 @@
 """Batched stepping: lattices advanced together by one fused launch per step
 must end bitwise where they end when stepped alone, whatever else is in the
-batch, through membership changes, graph-replayed chunks and odd step counts."""
+batch, through membership changes, graph-replayed chunks and odd step counts;
+and a member of a mixed batch must match the FP64 CPU oracle."""
 import numpy as np
 import pytest
 
@@ -177,3 +178,38 @@ def test_history_ring_matches_step_by_step_diagnostics(stream, batched):
         else:
             assert np.isnan(m)
     assert lbm.lbm_read_history(lat.h, 10)["step"][0] == 291
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_member_matches_oracle(orc, stream, prec):
+    """A member of a mixed batch (other sizes, Rayleigh numbers and strip
+    positions around it) against the oracle: T and f_l within 1e-5 (FP32),
+    every field within 1e-12 of its scale (FP64)."""
+    if prec == "fp32":
+        cases = [(256, 128, dict(Ra=1e6, strip_center=0.2))] + CASES[1:]
+        steps = 300
+    else:
+        cases = [(64, 32, dict()), (130, 70, dict(Ra=1e7, strip_center=0.5, strip_width=0.4, seed=9)),
+                 (67, 19, dict(Ra=1e5, strip_center=0.8))]
+        steps = 400
+    members = [make(stream, prec, nx, ny, kw) for nx, ny, kw in cases]
+    b = lbm.Batch(8, stream)
+    for lat in members:
+        b.add(lat)
+    b.step(steps)
+    for k in ((0,) if prec == "fp32" else range(len(cases))):
+        nx, ny, kw = cases[k]
+        ref = orc.Oracle(nx, ny, threads=8, **workloads.params(**kw))
+        ref.step(steps)
+        want, got = ref.fields(), members[k].fields()
+        if prec == "fp32":
+            for name in ("T", "fl"):
+                assert np.abs(got[name] - want[name]).max() <= 1e-5, (k, name)
+        else:
+            scale = {"H": 1.0, "T": 1.0, "fl": 1.0, "rho": 1.0, "ux": 0.1 / 3 ** 0.5, "uy": 0.1 / 3 ** 0.5}
+            for name, sc in scale.items():
+                err = np.abs(got[name] - want[name]).max() / max(np.abs(want[name]).max(), sc)
+                assert err <= 1e-12, (k, name, err)
+        d, dr = members[k].diagnostics(), ref.diagnostics()
+        assert d["step"] == steps
+        assert d["Q_cum"] == pytest.approx(dr["Q_cum"], rel=1e-5 if prec == "fp32" else 1e-12)

@@ -175,6 +175,47 @@ def test_stefan_fp64_field_parity(orc, stream):
     assert lat.diagnostics()["front_x"] == pytest.approx(ref.diagnostics()["front_x"], rel=1e-12)
 
 
+def fp32_drift_bound(n, H_max):
+    """Four standard deviations of the enthalpy drift that FP32 storage of the
+    populations allows after n steps: each step rounds the stored values once,
+    so the error of a cell's H walks randomly with steps of about
+    ulp(H_max) / sqrt(12) -- the latent-heat population g_0 ~ f_l L dominates
+    H_max = 1 + L.  For the 64 x 32 cavity (L = 1) at 1000 steps this is
+    8.7e-6, inside the 1e-5 bar; after 1e4 steps it is 2.8e-5 at Ste 1 and
+    1.1e-4 at Ste 0.1 (L = 10)."""
+    ulp = 2.0 ** (math.floor(math.log2(H_max)) - 23)
+    return 4.0 * math.sqrt(n) * ulp / math.sqrt(12.0)
+
+
+@pytest.mark.parametrize("Ste", [0.1, 1.0])
+def test_stefan_fp32_field_parity_1e4_steps(orc, stream, Ste):
+    """The FP32 path over 1e4 steps of the 1024 x 4 Stefan problem, cell by
+    cell against the oracle.  T everywhere within the FP32 storage drift
+    bound.  The phase field: the same cells solid, mushy and liquid; in the
+    mushy cell f_l is the heat that has crossed into it from its liquid
+    neighbour (at T_n above T_m) divided by L, so a drift dT of that
+    neighbour's temperature is a relative error dT / T_n of the flux it
+    integrates, and the same error in f_l (Stefan condition, Eqs. 7-8)."""
+    nx, ny, p = workloads.stefan_1024x4(Ste=Ste)
+    n = 10000
+    ref, lat = run_pair(orc, nx, ny, p, n, "fp32", stream, threads=8)
+    got, want = lat.fields(("H", "T", "fl")), ref.fields()
+    tol_T = max(1e-5, fp32_drift_bound(n, 1.0 + 1.0 / Ste))
+    e = np.abs(got["T"] - want["T"]).max()
+    assert e <= tol_T, f"T: max-abs error {e:.3e} > {tol_T:.3e}"
+    fl, flr = got["fl"], want["fl"]
+    assert np.array_equal(fl == 0.0, flr == 0.0) and np.array_equal(fl == 1.0, flr == 1.0)
+    front_err = 0.0
+    for row in range(ny):
+        (mushy,) = np.nonzero((flr[row] > 0.0) & (flr[row] < 1.0))
+        assert mushy.size == 1 and mushy[0] > 0
+        x = mushy[0]
+        tol_fl = tol_T / want["T"][row, x - 1]
+        assert abs(fl[row, x] - flr[row, x]) <= tol_fl, (row, fl[row, x] - flr[row, x], tol_fl)
+        front_err = max(front_err, tol_fl)
+    assert lat.diagnostics()["front_x"] == pytest.approx(ref.diagnostics()["front_x"], abs=front_err)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("Ste", [0.1, 1.0])
 def test_stefan_front_matches_neumann(orc, stream, prec, Ste):

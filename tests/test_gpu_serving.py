@@ -1,6 +1,6 @@
 """Continuous-batching server: every result is the one the request gets when
-solved alone; admission respects the HBM budget; a failing request does not
-disturb the others."""
+solved alone and, for the small FP32 requests, the oracle's; admission
+respects the HBM budget; a failing request does not disturb the others."""
 import numpy as np
 import pytest
 
@@ -94,3 +94,25 @@ def test_failed_request_is_isolated(stream):
         assert seen == 3
     finally:
         srv.close()
+
+
+def test_served_fp32_results_match_oracle(orc):
+    """Requests served together with others (mixed sizes, precisions and
+    Rayleigh numbers): every small FP32 one ends, field by field, within 1e-5
+    of the oracle in T and f_l."""
+    reqs = small_stream(10, 300)
+    results, _ = serving.serve(reqs, 8 * 2 ** 30, quantum=100, keep_fields=True)
+    by_id = {r.rid: r for r in reqs}
+    checked = 0
+    for x in results:
+        r = by_id[x.rid]
+        if r.precision != "fp32" or r.nx * r.ny > 256 * 128:
+            continue
+        ref = orc.Oracle(r.nx, r.ny, threads=8, **r.params())
+        ref.step(r.steps)
+        want = ref.fields()
+        for name in ("T", "fl"):
+            assert np.abs(x.fields[name] - want[name]).max() <= 1e-5, (r.rid, name)
+        assert x.diag["Q_cum"] == pytest.approx(ref.diagnostics()["Q_cum"], rel=1e-5)
+        checked += 1
+    assert checked >= 1
