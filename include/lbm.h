@@ -53,7 +53,7 @@ enum {
     LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                       */
     LBM_ERR_DIVERGED = -4, /* a non-finite H or rho was found by the diagnostics */
     LBM_ERR_STATE = -5,    /* call not valid in the handle's current state     */
-    LBM_ERR_TIMEOUT = -6   /* reserved: a bounded device wait ran out          */
+    LBM_ERR_TIMEOUT = -6   /* a bounded device wait ran out (staged sweep)     */
 };
 
 /* Storage and arithmetic precision of the populations.  The 16-bit modes
@@ -172,6 +172,33 @@ int lbm_set_diag_every(lbm_handle h, long long k);
  * follow the grouping of cells, to within FP64 rounding.  Errors: LBM_ERR_ARG. */
 int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int graph_chunk);
 
+/* Sweep kernel for 16-bit storage.  The staged sweep (an option for LBM_FP16,
+ * LBM_BF16, LBM_FP16_SR and LBM_BF16_SR; off by default) gives each block a band of
+ * consecutive rows of one 128-cell tile column and streams the tile rows it
+ * needs through a ring of shared-memory slots with TMA bulk copies, two rows
+ * ahead of the row it computes, so that the loads are in flight while it
+ * collides; it reads the 16-bit populations at the same addresses and
+ * computes exactly what the row-per-block sweep computes.  On GB300 it is
+ * slower than the row-per-block sweep (the 16-bit sweep is bound by
+ * instruction issue, not by memory latency, and each tile row takes 27 bulk
+ * copies), so it is off by default.  bands: -1 = automatic (as many bands
+ * per tile column as give one wave of 8 blocks per SM, each at least 4 rows),
+ * 0 = the row-per-block sweep (lbm_set_launch shape; the default), n > 0 = n
+ * bands per tile column (capped at ny / 4).  FP32 and FP64 lattices always
+ * take the row-per-block sweep.  Results do not depend on it.
+ * Errors: LBM_ERR_ARG. */
+int lbm_set_staging(lbm_handle h, int bands);
+
+/* Every wait of the staged sweep on its shared-memory ring is bounded: after
+ * tries + 1 unsuccessful tries (default 2^20, about a second) the block
+ * records a timeout, waits for its copies still in flight and returns, and
+ * the next lbm_diagnostics reports LBM_ERR_TIMEOUT; the state is then invalid
+ * until lbm_set_params or lbm_write_populations.  force_timeout = 1 makes
+ * every block first wait on a barrier that nothing completes, so that the
+ * timeout path can be tested without a fault (0 for normal operation).
+ * Errors: LBM_ERR_ARG. */
+int lbm_set_wait_limit(lbm_handle h, long long tries, int force_timeout);
+
 /* Counters of how the handle's sweeps were enqueued since lbm_create:
  * launched directly, replayed from captured graphs, and graphs captured. */
 typedef struct {
@@ -207,7 +234,8 @@ int lbm_read_fields(lbm_handle h, unsigned mask, double *H, double *T, double *f
                     double *ux, double *uy, double *rho);
 
 /* Diagnostics record of the current step.  Synchronises.  Returns
- * LBM_ERR_DIVERGED (with *out filled) if nan_flag is set. */
+ * LBM_ERR_DIVERGED (with *out filled) if nan_flag is set, LBM_ERR_TIMEOUT if a
+ * bounded device wait ran out since the state was last set. */
 int lbm_diagnostics(lbm_handle h, lbm_diag *out);
 
 /* History of the run (the melt-fraction and Nusselt histories of Sec. 3.2):

@@ -79,6 +79,14 @@ struct lbm_s {
     lbm_derived d{};
     int lo2 = 0, hi2 = -1, strip_on = 0;
     dim3 block, grid;
+    // staged sweep (16-bit storage): bands per tile column (-1: one wave of
+    // blocks, 0: the row-per-block sweep), its grid and heated-wall partials
+    int staged_mode = 0;
+    int num_sms = 152;
+    dim3 sgrid;
+    int snq = 0;
+    long long wait_limit = 1ll << 20;
+    int force_timeout = 0;
     // scratch: reduction partials, tickets, record; allocated once
     void *scratch = nullptr;
     double *qpart = nullptr, *dpart = nullptr, *dpart2 = nullptr;
@@ -157,12 +165,25 @@ size_t buffer_bytes(const lbm_s *h) {
     return (size_t)h->ntx * (size_t)h->ny * (size_t)kRS * h->esize;
 }
 
+// Resident blocks per SM of the staged sweep (128 threads, 64 registers,
+// about 25 KB of shared memory each).
+constexpr int kStagedBlocksPerSM = 8;
+
+bool use_staged(const lbm_s *h) { return h->esize == 2 && h->staged_mode != 0; }
+
 void set_grid(lbm_s *h) {
     h->block = dim3(kTW);
     h->grid = dim3(h->ntx, (h->ny + h->rows - 1) / h->rows);
     // blocks that fold the heated-wall inflow: the bottom row band of every
     // tile column (cavity) or the first tile column of every row band (Stefan)
     h->nq = h->p.problem == LBM_CAVITY ? (int)h->grid.x : (int)h->grid.y;
+    // Staged sweep: bands of consecutive rows per tile column, as many as fill
+    // the GPU with one wave of blocks, each band at least 4 rows high.
+    int bands = h->staged_mode > 0 ? h->staged_mode
+                                   : (h->num_sms * kStagedBlocksPerSM + h->ntx - 1) / h->ntx;
+    bands = std::max(1, std::min(bands, std::max(1, h->ny / 4)));
+    h->sgrid = dim3(h->ntx, bands);
+    h->snq = h->p.problem == LBM_CAVITY ? (int)h->sgrid.x : (int)h->sgrid.y;
 }
 
 double *staging(lbm_s *h) {
@@ -204,6 +225,9 @@ SweepArgs<real> make_args(const lbm_s *h, const void *src, void *dst) {
     a.hist = h->hist;
     a.hist_cap = h->hist_cap;
     a.step = h->step;
+    a.staged = 0;
+    a.force_timeout = h->force_timeout;
+    a.wait_limit = h->wait_limit;
     return a;
 }
 
@@ -269,8 +293,13 @@ int launch_one(lbm_s *h, bool diag) {
     const long long next = h->step + 1;
     SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
     a.step = next;
+    const bool staged = use_staged(h);
+    if (staged) {
+        a.staged = 1;
+        a.nq = h->snq;
+    }
     cudaError_t e = launch_lattice<real, S>(a, h->p.problem, h->p.flow_on != 0, diag ? kSweepDiag : kSweep,
-                                         h->grid, h->block, h->stream, true);
+                                         staged ? h->sgrid : h->grid, h->block, h->stream, true);
     if (e != cudaSuccess) return set_err(h, LBM_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(e));
     h->cur ^= 1;
     h->has_prev = true;
@@ -465,6 +494,10 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     h->nx = nx;
     h->ny = ny;
     h->precision = precision;
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        h->num_sms = 152;
+    }
     h->esize = precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
     h->ntx = (nx + kTW - 1) / kTW;
     if (h->esize == 2) h->prefetch = kDefaultPrefetch16;
@@ -625,7 +658,28 @@ int lbm_diagnostics(lbm_handle h, lbm_diag *out) {
     out->front_x = r.melt_sum / (double)h->ny;
     out->max_u = r.max_u;
     out->nan_flag = r.nan_flag != 0.0 ? 1 : 0;
+    if (r.timeout != 0.0)
+        return set_err(h, LBM_ERR_TIMEOUT,
+                       "a bounded device wait of the staged sweep ran out; the populations since are not "
+                       "valid (lbm_set_params or lbm_write_populations resets the state)");
     if (out->nan_flag) return set_err(h, LBM_ERR_DIVERGED, "non-finite H or rho at step %lld", h->step);
+    return LBM_OK;
+}
+
+int lbm_set_staging(lbm_handle h, int bands) {
+    if (!h || bands < -1 || bands > 65535) return set_err(h, LBM_ERR_ARG, "bands must be -1, 0 or 1..65535");
+    drop_graphs(h);
+    h->staged_mode = bands;
+    set_grid(h);
+    return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_handle h, long long tries, int force_timeout) {
+    if (!h || tries < 0 || (force_timeout != 0 && force_timeout != 1))
+        return set_err(h, LBM_ERR_ARG, "tries must be >= 0 and force_timeout 0 or 1");
+    drop_graphs(h);
+    h->wait_limit = tries;
+    h->force_timeout = force_timeout;
     return LBM_OK;
 }
 
@@ -666,8 +720,8 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
     h->step = step;
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
-    const double counter = (double)step;
-    CUDA_TRY(h, cudaMemcpyAsync(&h->rec->counter, &counter, sizeof(double), cudaMemcpyHostToDevice,
+    const unsigned long long counter = (unsigned long long)step;
+    CUDA_TRY(h, cudaMemcpyAsync(&h->rec->counter, &counter, sizeof(counter), cudaMemcpyHostToDevice,
                                 h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
@@ -1269,10 +1323,10 @@ extern "C" int lbm_step_static(const void *src, void *dst, int nx, int ny, int p
 
     // The array keeps the previous call's contents: the tickets and the record
     // must start from zero, and the record's step counter from `step`.
-    const double counter = (double)step;
+    const unsigned long long counter = (unsigned long long)step;
     e = cudaMemsetAsync(base, 0, kStaticOffQ, t.stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&t.rec->counter, &counter, sizeof(double), cudaMemcpyHostToDevice, t.stream);
+        e = cudaMemcpyAsync(&t.rec->counter, &counter, sizeof(counter), cudaMemcpyHostToDevice, t.stream);
     if (e != cudaSuccess)
         return set_err(nullptr, LBM_ERR_CUDA, "lbm_step_static: clearing the scratch failed: %s",
                        cudaGetErrorString(e));

@@ -41,9 +41,13 @@ struct DevRecord {
     double max_u;     // max |u|
     double nan_flag;  // 1 if a non-finite H or rho was seen
     double valid;     // 1 once the fields of `step` have been reduced
-    double counter;   // steps taken: advanced by every sweep on the device, so
-                      // that replayed CUDA graphs stamp records correctly
-    double rng[2];    // stochastic-rounding step seeds, one word per buffer parity
+    unsigned long long counter;  // steps taken: advanced by every sweep on the
+                                 // device, so that replayed CUDA graphs stamp
+                                 // records correctly (an integer: GB300's FP64
+                                 // pipe is narrow, and a sweep's warps would
+                                 // each issue the predicated FP64 add)
+    unsigned long long rng[2];   // stochastic-rounding step seeds, one word per buffer parity
+    double timeout;   // 1 once a bounded device wait ran out (staged sweep)
 };
 
 // Arguments of every lattice kernel, passed by value.
@@ -83,6 +87,13 @@ struct SweepArgs {
     long long hist_cap;
     long long step;        // step index the launch produces (host bookkeeping only;
                            // the record takes its step from rec->counter)
+    // staged sweep (16-bit storage): 1 = launch staged_kernel over the band
+    // grid; its mbarrier waits give up after wait_limit + 1 tries, and
+    // force_timeout = 1 makes each block first wait on a barrier that nothing
+    // completes (tests of the timeout path)
+    int staged;
+    int force_timeout;
+    long long wait_limit;
     // field outputs (kFields), nx*ny doubles each, row-major; NULL = skip
     double *oH, *oT, *oFL, *oUX, *oUY, *oRHO;
 };

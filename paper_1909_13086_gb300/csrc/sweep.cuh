@@ -163,6 +163,13 @@ struct Store<F16<SR>> {
         *pg = __ushort_as_half((unsigned short)(d >> 16));
         *pf = __ushort_as_half((unsigned short)(d & 0xffffu));
     }
+    // a (g, f) word of the paired layout: g in the high half, f in the low one
+    __device__ static float hi(uint32_t u) { return __half2float(__ushort_as_half((unsigned short)(u >> 16))); }
+    __device__ static float lo(uint32_t u) { return __half2float(__ushort_as_half((unsigned short)(u & 0xffffu))); }
+    __device__ static uint32_t pack_rn(float g, float f) {
+        return ((uint32_t)__half_as_ushort(__float2half_rn(g)) << 16) | __half_as_ushort(__float2half_rn(f));
+    }
+    __device__ static uint32_t pack_sr(float g, float f, uint32_t rbits) { return cvt_rs_f16x2(g, f, rbits); }
 };
 // BF16 has FP32's exponent range, so no scaling; 16 bits are discarded.
 template <bool SR>
@@ -189,7 +196,37 @@ struct Store<BF16<SR>> {
         *pg = __ushort_as_bfloat16((unsigned short)(d >> 16));
         *pf = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
     }
+    // a (g, f) word of the paired layout: a BF16 value is the top half of a float
+    __device__ static float hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+    __device__ static float lo(uint32_t u) { return __uint_as_float(u << 16); }
+    __device__ static uint32_t pack_rn(float g, float f) {
+        return ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(g)) << 16) |
+               __bfloat16_as_ushort(__float2bfloat16_rn(f));
+    }
+    __device__ static uint32_t pack_sr(float g, float f, uint32_t rbits) { return cvt_rs_bf16x2(g, f, rbits); }
 };
+// Where plane p (0..8: f_0..f_8, 9..17: g_0..g_8) of the cell in column lx of
+// a tile row lives, counted in elements from the row's first one.  FP32 /
+// FP64: plane after plane, kTW values each (lbm_internal.h).  16-bit storage:
+// f_i and g_i, which stream from the same source cell, share one 32-bit word
+// -- f_i in the low half, g_i in the high half -- and the nine words of the
+// directions follow one another kTW at a time, so that one 32-bit load and one
+// 32-bit store move both populations of a direction.  A tile row holds the
+// same 18 kTW values either way.
+template <typename S>
+__host__ __device__ constexpr int plane_ofs(int p, int lx) {
+    return Store<S>::kDev ? 2 * ((p % 9) * kTW + lx) + (p >= 9 ? 1 : 0) : p * kTW + lx;
+}
+template <typename S>
+__host__ __device__ inline long long cell_index(int x, int y, int p, int ny) {
+    return ((long long)(x / kTW) * ny + y) * kRS + plane_ofs<S>(p, x % kTW);
+}
+// Elements from one column to the next within a plane (2 in the paired layout).
+template <typename S>
+__host__ __device__ constexpr int col_step() {
+    return Store<S>::kDev ? 2 : 1;
+}
+
 // Offset added to a stored f value (plane i) to recover f_i.
 template <typename real, typename S>
 __device__ __forceinline__ real f_ofs(int i) {
@@ -393,6 +430,42 @@ __device__ __forceinline__ void pull_fast(const typename Store<S>::elem *__restr
                                           const typename Store<S>::elem *__restrict__ bL,
                                           const typename Store<S>::elem *__restrict__ bR, real f[9],
                                           real g[9]) {
+    if constexpr (Store<S>::kDev) {
+        // paired layout: word i of a cell holds (g_i, f_i); a row is kRS / 2
+        // words, a direction's words kTW apart
+        constexpr int R = kRS / 2, W = kTW;
+        if (FLOW) {
+            const uint32_t *w = reinterpret_cast<const uint32_t *>(b);
+            const uint32_t *wl = reinterpret_cast<const uint32_t *>(bL);
+            const uint32_t *wr = reinterpret_cast<const uint32_t *>(bR);
+            uint32_t u[9];
+            u[0] = __ldg(w + 0 * W);
+            u[1] = __ldg(wl + 1 * W - 1);
+            u[2] = __ldg(w + 2 * W - R);
+            u[3] = __ldg(wr + 3 * W + 1);
+            u[4] = __ldg(w + 4 * W + R);
+            u[5] = __ldg(wl + 5 * W - R - 1);
+            u[6] = __ldg(wr + 6 * W - R + 1);
+            u[7] = __ldg(wr + 7 * W + R + 1);
+            u[8] = __ldg(wl + 8 * W + R - 1);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f[i] = Store<S>::lo(u[i]);
+                g[i] = Store<S>::hi(u[i]);
+            }
+        } else {  // the high halves only: element 2 * word + 1
+            g[0] = Store<S>::ldr(b + 2 * (0 * W) + 1);
+            g[1] = Store<S>::ldr(bL + 2 * (1 * W - 1) + 1);
+            g[2] = Store<S>::ldr(b + 2 * (2 * W - R) + 1);
+            g[3] = Store<S>::ldr(bR + 2 * (3 * W + 1) + 1);
+            g[4] = Store<S>::ldr(b + 2 * (4 * W + R) + 1);
+            g[5] = Store<S>::ldr(bL + 2 * (5 * W - R - 1) + 1);
+            g[6] = Store<S>::ldr(bR + 2 * (6 * W - R + 1) + 1);
+            g[7] = Store<S>::ldr(bR + 2 * (7 * W + R + 1) + 1);
+            g[8] = Store<S>::ldr(bL + 2 * (8 * W + R - 1) + 1);
+        }
+        return;
+    }
     constexpr int R = kRS, W = kTW;
 #define BTRIRT_PULL(P, arr, LD)                             \
     arr[0] = LD<real, S>(b + (P + 0) * W, 0);               \
@@ -415,26 +488,39 @@ __device__ __forceinline__ void pull_fast(const typename Store<S>::elem *__restr
 // of an interior row, after pull_fast: the directions whose source lies beyond
 // x = 0 (c_x = +1: 1, 5, 8) or beyond x = nx - 1 (c_x = -1: 3, 6, 7) take the
 // cell's own post-collision opposite populations, as pull_any does.
+// The cell's own post-collision populations of direction o (b points at the
+// cell's element of plane 0).
+template <typename real, typename S, bool FLOW>
+__device__ __forceinline__ void load_own(const typename Store<S>::elem *b, int o, real &f, real &g) {
+    if constexpr (Store<S>::kDev) {
+        if (FLOW) {
+            const uint32_t u = __ldg(reinterpret_cast<const uint32_t *>(b) + o * kTW);
+            f = Store<S>::lo(u);
+            g = Store<S>::hi(u);
+        } else {
+            g = Store<S>::ldr(b + 2 * o * kTW + 1);
+        }
+    } else {
+        g = ld_g<real, S>(b + (9 + o) * kTW, o);
+        if (FLOW) f = ld_f<real, S>(b + o * kTW, o);
+    }
+}
+
 template <typename real, typename S, bool FLOW>
 __device__ __forceinline__ void bounce_side_walls(const typename Store<S>::elem *b, int x, int nx,
                                                   real f[9], real g[9]) {
-    constexpr int W = kTW;
     if (x == 0) {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (cx_of(i) != 1) continue;
-            const int o = opp_of(i);
-            g[i] = ld_g<real, S>(b + (9 + o) * W, o);
-            if (FLOW) f[i] = ld_f<real, S>(b + o * W, o);
+            load_own<real, S, FLOW>(b, opp_of(i), f[i], g[i]);
         }
     }
     if (x == nx - 1) {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (cx_of(i) != -1) continue;
-            const int o = opp_of(i);
-            g[i] = ld_g<real, S>(b + (9 + o) * W, o);
-            if (FLOW) f[i] = ld_f<real, S>(b + o * W, o);
+            load_own<real, S, FLOW>(b, opp_of(i), f[i], g[i]);
         }
     }
 }
@@ -442,19 +528,20 @@ __device__ __forceinline__ void bounce_side_walls(const typename Store<S>::elem 
 // Any cell: explicit source test per direction and the wall rules.
 template <typename real, typename S, int PROB, bool FLOW>
 __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y, real f[9],
-                                         real g[9], real &q) {
+                                         real g[9], double &q) {
     const auto *src = static_cast<const typename Store<S>::elem *>(a.src);
-    const long long self = pop_index(x, y, 0, a.ny);
+    const long long self = cell_index<S>(x, y, 0, a.ny);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int cx = cx_of(i), cy = cy_of(i);
         int sx = x - cx, sy = y - cy;
         if (PROB == kStefan) sy = (sy < 0) ? sy + a.ny : ((sy >= a.ny) ? sy - a.ny : sy);
         const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
-        const long long cell = in ? pop_index(sx, sy, 0, a.ny) : self;
+        const long long cell = in ? cell_index<S>(sx, sy, 0, a.ny) : self;
         const int pl = in ? i : opp_of(i);
-        real gv = ld_g<real, S>(src + cell + (9 + pl) * kTW, pl);
-        if (FLOW) f[i] = ld_f<real, S>(src + cell + pl * kTW, pl);
+        real gv, fv = real(0);
+        load_own<real, S, FLOW>(src + cell, pl, fv, gv);
+        if (FLOW) f[i] = fv;
         if (!in) {
             bool heated;
             if (PROB == kStefan) {
@@ -466,7 +553,7 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
             if (heated) {
                 // 2 w_i C_p T_h (T_h = 1), in g's stored units; q is physical
                 const real wt = real(2) * w_of<real>(i) * real(Store<S>::kG);
-                q += (wt - real(2) * gv) * (real(1) / real(Store<S>::kG));
+                q += (double)((wt - real(2) * gv) * (real(1) / real(Store<S>::kG)));
                 gv = wt - gv;
             }
         }
@@ -642,7 +729,7 @@ __global__ void __launch_bounds__(kReduceThreads)
     for (int k = 0; k < 4; ++k) acc[k] = kind[k] ? warp_max(acc[k]) : warp_sum(acc[k]);
     block_fold<4, A>(acc, kind, sh);
     if (threadIdx.x == 0) {
-        rec->step = init ? 0.0 : rec->counter;
+        rec->step = init ? 0.0 : (double)rec->counter;
         rec->melt_sum = dec_sum(acc[0]);
         rec->H_sum = dec_sum(acc[1]);
         rec->max_u = dec_max(acc[2]);
@@ -651,7 +738,7 @@ __global__ void __launch_bounds__(kReduceThreads)
         if (init) {
             rec->Q_last = 0.0;
             rec->Q_cum = 0.0;
-            rec->counter = 0.0;
+            rec->counter = 0ull;
         }
         *ticket = 0u;
         if (hist && !init) hist_put(hist, hist_cap, rec, ncells);
@@ -670,108 +757,101 @@ __device__ __forceinline__ void prefetch_tile_row_l2(const E *p) {
 }
 
 // ---- the sweep ----
-// One block's work: the tile column bx (kTW cells) and the row band by
-// (a.rows rows) of the lattice described by a; gx is the number of tile
-// columns (for the block's partial-sum slot).  Called by lattice_kernel (one
-// lattice, bx = blockIdx.x) and batch_kernel (a block of a batch of lattices).
-template <typename real, typename S, int PROB, bool FLOW, int MODE>
-__device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int bx, const int by,
-                                            const int gx, double *sh) {
-    using E = typename Store<S>::elem;
-    const E *src = static_cast<const E *>(a.src);
-    const int lx = threadIdx.x;
-    const int x = bx * kTW + lx;
-    const int y0 = by * a.rows;
-    const int y1 = min(y0 + a.rows, a.ny);
-    // Blocks are scheduled roughly in row order, so the row `prefetch` rows
-    // ahead belongs to a block that starts a little later: fetching it into L2
-    // now shortens that block's load latency.
-    if (a.prefetch > 0 && threadIdx.x == 0 && y0 + a.prefetch < a.ny)
-        prefetch_tile_row_l2(src + pop_index(bx * kTW, y0 + a.prefetch, 0, a.ny));
-    // the device-side step counter (read by the diagnostics fold after this launch)
-    if (MODE != kFields && threadIdx.x == 0 && bx == 0 && by == 0) a.rec->counter += 1.0;
-    // Stochastic rounding seed of this step: read from the word of the source
-    // buffer's parity; block (0, 0) hands the next value to the other word,
-    // which only the next step reads -- no race, and graph replays see a new
-    // seed every step.
+// Per-step bookkeeping at a block's start: the device-side step counter
+// (advanced by block (0, 0); read by the diagnostics fold after this launch)
+// and the stochastic-rounding seed of this step, read from the word of the
+// source buffer's parity -- block (0, 0) hands the next value to the other
+// word, which only the next step reads: no race, and graph replays see a new
+// seed every step.
+template <typename real, typename S, int MODE>
+__device__ __forceinline__ uint32_t step_prologue(const SweepArgs<real> &a, int bx, int by) {
+    if (MODE != kFields && threadIdx.x == 0 && bx == 0 && by == 0) a.rec->counter += 1ull;
     uint32_t step_seed = 0;
     if (Store<S>::kSR && MODE != kFields) {
-        const double sd = a.rec->rng[a.parity];
-        if (threadIdx.x == 0 && bx == 0 && by == 0) a.rec->rng[a.parity ^ 1] = sd + 1.0;
-        step_seed = hash32((uint32_t)(unsigned long long)sd ^ 0x5bd1e995u);
+        const unsigned long long sd = a.rec->rng[a.parity];
+        if (threadIdx.x == 0 && bx == 0 && by == 0) a.rec->rng[a.parity ^ 1] = sd + 1ull;
+        step_seed = hash32((uint32_t)sd ^ 0x5bd1e995u);
     }
-    const bool active = x < a.nx;
-    // the warp's 32 columns are clear of both side walls (warp-uniform)
-    const int xw = bx * kTW + (lx & ~31);
-    const bool fastcol = xw >= 1 && xw + 31 <= a.nx - 2;
-    // A cavity warp that touches a side wall also takes the fast loads on the
-    // interior rows: the wall lane's out-of-lattice neighbour pointer is
-    // clamped to its own cell (the loads then stay inside its tile row) and
-    // its wall directions are replaced by bounce-back afterwards.
-    const bool sidewall = PROB == kCavity && !fastcol;
+    return step_seed;
+}
 
-    long long i0 = 0, iL = 0, iR = 0;
-    if (fastcol || sidewall) {
-        i0 = pop_index(x, y0, 0, a.ny);
-        iL = (lx == 0 && x > 0) ? pop_index(x - 1, y0, 0, a.ny) + 1 : i0;
-        iR = (lx == kTW - 1 && x < a.nx - 1) ? pop_index(x + 1, y0, 0, a.ny) - 1 : i0;
-    }
-
-    real q = real(0), umax2 = real(0);
+// Diagnostics accumulators of one thread.
+// The heated-wall inflow is summed in FP64 from the first crossing on: a sum
+// of a band's working-precision terms is then exact, so the flux does not
+// depend on how many rows a block covers.
+template <typename real>
+struct CellSums {
+    double q = 0.0;
+    real umax2 = real(0);
     typename DiagAcc<real>::T sfl = 0, sH = 0;
     bool bad = false;
-    for (int y = y0; y < y1; ++y, i0 += kRS, iL += kRS, iR += kRS) {
-        if (!active) continue;
-        real f[9], g[9];
-        if ((fastcol || sidewall) && y >= 1 && y <= a.ny - 2) {
-            pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
-            if (sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
-        } else {
-            pull_any<real, S, PROB, FLOW>(a, x, y, f, g, q);
-        }
-        if (MODE == kFields) {
-            const Macro<real> m = cell_update<real, S, FLOW, false>(a, f, g);
-            const long long o = (long long)y * a.nx + x;
-            if (a.oH) a.oH[o] = (double)m.H;
-            if (a.oT) a.oT[o] = (double)m.T;
-            if (a.oFL) a.oFL[o] = (double)m.fl;
-            if (a.oUX) a.oUX[o] = (double)m.ux;
-            if (a.oUY) a.oUY[o] = (double)m.uy;
-            if (a.oRHO) a.oRHO[o] = (double)m.rho;
-            continue;
-        }
-        const Macro<real> m = cell_update<real, S, FLOW, true>(a, f, g);
-        E *d = static_cast<E *>(a.dst) + pop_index(x, y, 0, a.ny);
+};
+
+// Collide the pulled populations of cell (x, y) and store them at element
+// offset c (cell_index(x, y, 0)) of the destination (MODE == kFields: write
+// the fields instead).
+template <typename real, typename S, bool FLOW, int MODE>
+__device__ __forceinline__ void finish_cell(const SweepArgs<real> &a, int x, int y, long long c, real f[9],
+                                            real g[9], uint32_t step_seed, CellSums<real> &acc) {
+    using E = typename Store<S>::elem;
+    if (MODE == kFields) {
+        const Macro<real> m = cell_update<real, S, FLOW, false>(a, f, g);
+        const long long o = (long long)y * a.nx + x;
+        if (a.oH) a.oH[o] = (double)m.H;
+        if (a.oT) a.oT[o] = (double)m.T;
+        if (a.oFL) a.oFL[o] = (double)m.fl;
+        if (a.oUX) a.oUX[o] = (double)m.ux;
+        if (a.oUY) a.oUY[o] = (double)m.uy;
+        if (a.oRHO) a.oRHO[o] = (double)m.rho;
+        return;
+    }
+    const Macro<real> m = cell_update<real, S, FLOW, true>(a, f, g);
+    E *d = static_cast<E *>(a.dst) + c;
+    if constexpr (Store<S>::kDev) {
+        // paired layout: one 32-bit (g_i, f_i) word per direction; without
+        // flow only the g halves are written
+        uint32_t *dw = reinterpret_cast<uint32_t *>(d);
         if (!Store<S>::kSR || (!FLOW && !(isfinite(m.H) && isfinite(m.rho)))) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                Store<S>::str_rn(d + (9 + i) * kTW, g[i]);
-                if (FLOW) Store<S>::str_rn(d + i * kTW, f[i]);
+                if (FLOW) dw[i * kTW] = Store<S>::pack_rn(g[i], f[i]);
+                else Store<S>::str_rn(d + 2 * i * kTW + 1, g[i]);
             }
         } else {
             uint32_t rs = hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x));
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                if (FLOW)
-                    Store<S>::st2r(d + (9 + i) * kTW, d + i * kTW, g[i], f[i], lcg_next32(rs));
-                else
-                    Store<S>::strs(d + (9 + i) * kTW, g[i], lcg_next(rs));
+                if (FLOW) dw[i * kTW] = Store<S>::pack_sr(g[i], f[i], lcg_next32(rs));
+                else Store<S>::strs(d + 2 * i * kTW + 1, g[i], lcg_next(rs));
             }
         }
-        if (MODE == kSweepDiag) {
-            sfl += enc_sum(m.fl);
-            sH += enc_sum(m.H);
-            umax2 = max(umax2, m.ux * m.ux + m.uy * m.uy);
-            bad |= !(isfinite(m.H) && isfinite(m.rho));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            Store<S>::str_rn(d + (9 + i) * kTW, g[i]);
+            if (FLOW) Store<S>::str_rn(d + i * kTW, f[i]);
         }
     }
-    if (MODE == kFields) return;
+    if (MODE == kSweepDiag) {
+        acc.sfl += enc_sum(m.fl);
+        acc.sH += enc_sum(m.H);
+        acc.umax2 = max(acc.umax2, m.ux * m.ux + m.uy * m.uy);
+        acc.bad |= !(isfinite(m.H) && isfinite(m.rho));
+    }
+}
 
-    // ---- heated-wall inflow of this step (blocks touching the T_h wall) ----
+// A block's end: the heated-wall inflow of this step (blocks touching the T_h
+// wall: the cavity's bottom row band, the Stefan problem's first tile column),
+// folded by the last such block to take a ticket, and the diagnostics
+// partials.  bx, by: the block's tile column and row band; gx: tile columns.
+template <typename real, int PROB, int MODE>
+__device__ __forceinline__ void block_epilogue(const SweepArgs<real> &a, int bx, int by, int gx,
+                                               const CellSums<real> &acc, double *sh) {
+    if (MODE == kFields) return;
     const bool qblock = (PROB == kCavity) ? (a.strip_on && by == 0) : (bx == 0);
     if (qblock) {
         const int kind[1] = {0};
-        double v[1] = {warp_sum((double)q)};
+        double v[1] = {warp_sum(acc.q)};
         block_fold<1>(v, kind, sh);
         __shared__ bool qlast;
         if (threadIdx.x == 0) {
@@ -792,7 +872,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
                 a.rec->Q_cum += v[0];
                 *a.qcount = 0u;
                 if (a.hist) {  // this step's inflow; the melt fraction comes with diagnostics
-                    const long long st = (long long)__ldcg(&a.rec->counter);
+                    const long long st = (long long)__ldcg(&a.rec->counter);  // integer load
                     double *e = a.hist + 4 * (st % a.hist_cap);
                     e[0] = (double)st;
                     e[1] = v[0];
@@ -801,11 +881,61 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
             }
         }
     }
-
     // ---- diagnostics: sums within the warp in the working precision (32
-    // threads x `rows` cells), then FP64 across warps and blocks ----
+    // threads x their cells), then FP64 across warps and blocks ----
     if (MODE == kSweepDiag)
-        diag_partial<real>(sfl, sH, umax2, bad, a.dpart, (size_t)bx + (size_t)by * gx, sh);
+        diag_partial<real>(acc.sfl, acc.sH, acc.umax2, acc.bad, a.dpart, (size_t)bx + (size_t)by * gx, sh);
+}
+
+// One block's work: the tile column bx (kTW cells) and the row band by
+// (a.rows rows) of the lattice described by a; gx is the number of tile
+// columns (for the block's partial-sum slot).  Called by lattice_kernel (one
+// lattice, bx = blockIdx.x) and batch_kernel (a block of a batch of lattices).
+template <typename real, typename S, int PROB, bool FLOW, int MODE>
+__device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int bx, const int by,
+                                            const int gx, double *sh) {
+    using E = typename Store<S>::elem;
+    const E *src = static_cast<const E *>(a.src);
+    const int lx = threadIdx.x;
+    const int x = bx * kTW + lx;
+    const int y0 = by * a.rows;
+    const int y1 = min(y0 + a.rows, a.ny);
+    // Blocks are scheduled roughly in row order, so the row `prefetch` rows
+    // ahead belongs to a block that starts a little later: fetching it into L2
+    // now shortens that block's load latency.
+    if (a.prefetch > 0 && threadIdx.x == 0 && y0 + a.prefetch < a.ny)
+        prefetch_tile_row_l2(src + cell_index<S>(bx * kTW, y0 + a.prefetch, 0, a.ny));
+    const uint32_t step_seed = step_prologue<real, S, MODE>(a, bx, by);
+    const bool active = x < a.nx;
+    // the warp's 32 columns are clear of both side walls (warp-uniform)
+    const int xw = bx * kTW + (lx & ~31);
+    const bool fastcol = xw >= 1 && xw + 31 <= a.nx - 2;
+    // A cavity warp that touches a side wall also takes the fast loads on the
+    // interior rows: the wall lane's out-of-lattice neighbour pointer is
+    // clamped to its own cell (the loads then stay inside its tile row) and
+    // its wall directions are replaced by bounce-back afterwards.
+    const bool sidewall = PROB == kCavity && !fastcol;
+
+    long long i0 = cell_index<S>(x, y0, 0, a.ny), iL = i0, iR = i0;
+    if (fastcol || sidewall) {
+        constexpr int cs = col_step<S>();
+        iL = (lx == 0 && x > 0) ? cell_index<S>(x - 1, y0, 0, a.ny) + cs : i0;
+        iR = (lx == kTW - 1 && x < a.nx - 1) ? cell_index<S>(x + 1, y0, 0, a.ny) - cs : i0;
+    }
+
+    CellSums<real> acc;
+    for (int y = y0; y < y1; ++y, i0 += kRS, iL += kRS, iR += kRS) {
+        if (!active) continue;
+        real f[9], g[9];
+        if ((fastcol || sidewall) && y >= 1 && y <= a.ny - 2) {
+            pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
+            if (sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
+        } else {
+            pull_any<real, S, PROB, FLOW>(a, x, y, f, g, acc.q);
+        }
+        finish_cell<real, S, FLOW, MODE>(a, x, y, i0, f, g, step_seed, acc);
+    }
+    block_epilogue<real, PROB, MODE>(a, bx, by, gx, acc, sh);
 }
 
 // FP32 arithmetic: at least 8 blocks of 128 threads per SM (registers capped at
@@ -818,6 +948,253 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     pdl_launch_dependents();
     pdl_wait();  // the previous sweep's populations, tickets and record
     sweep_block<real, S, PROB, FLOW, MODE>(a, blockIdx.x, blockIdx.y, gridDim.x, sh);
+}
+
+// ---- the staged sweep (16-bit storage) ----
+// A block owns a band of consecutive rows of one tile column and streams the
+// tile rows it needs through a ring of kStSlots shared-memory slots, filled by
+// TMA bulk copies (cp.async.bulk, completion counted on one mbarrier per
+// slot) two rows ahead of the row being computed, so that the loads are in
+// flight while the block collides -- without holding registers.  A staged row
+// keeps, per direction, 4 words of the left neighbour tile, the tile's 128
+// words and 4 words of the right neighbour tile (each piece a 16-byte-aligned
+// bulk copy), so every lane reads its pull sources from shared memory at
+// uniform offsets.  Bands alternate direction (even bands top-down in y, odd
+// bottom-up), so that two bands reach the rows they share at the same time
+// and the second read of a halo row comes from L2.  Every wait is bounded:
+// when one runs out, the block records a timeout in the diagnostics record,
+// waits (bounded) for its copies still in flight and returns.
+constexpr int kStW = kTW + 8;        // words per direction in a staged row
+constexpr int kStRow = 9 * kStW;     // words per staged row
+constexpr int kStSlots = 5;          // ring depth: rows p, p + 1, p + 2 in use, 2 in flight
+constexpr size_t kStSmem = (size_t)kStSlots * kStRow * 4 + (kStSlots + 1) * 8;
+constexpr long long kStDrainLimit = 1ll << 22;  // tries per in-flight copy after a timeout
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of the given parity, trying at most limit + 1 times.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit) {
+    for (long long it = 0; it <= limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Global -> shared bulk copy; bytes and both addresses multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Staged row s of a band (y = ys0 + s dir) into slot s % kStSlots, issued by
+// warp 0.  Rows outside the cavity are not loaded (walls); their slot's phase
+// is completed by a plain arrival, so that every slot's phases keep counting
+// one per staged row.
+template <typename S, int PROB>
+__device__ __forceinline__ void stage_row(const void *srcv, int nx, int ny, int ntx, int bx, int ys0, int dir,
+                                          int s, uint32_t *rows, uint64_t *bar) {
+    const int lane = threadIdx.x & 31;
+    const int slot = s % kStSlots;
+    int y = ys0 + s * dir;
+    if (PROB == kStefan) y = (y % ny + ny) % ny;
+    if ((unsigned)y >= (unsigned)ny) {
+        if (lane == 0) mbar_arrive(bar + slot);
+        return;
+    }
+    const bool left = bx > 0, right = bx < ntx - 1;
+    if (lane == 0) {
+        // the slot was last read before the block barrier that preceded this
+        // call; order those reads before the asynchronous writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar + slot, 9u * 512u + (left ? 9u * 16u : 0u) + (right ? 9u * 16u : 0u));
+    }
+    __syncwarp();
+    const uint32_t *src = static_cast<const uint32_t *>(srcv);
+    constexpr long long kRowWords = kRS / 2;
+    uint32_t *dst = rows + (size_t)slot * kStRow;
+    (void)nx;
+    if (lane < 9) {
+        bulk_g2s(dst + lane * kStW + 4, src + ((long long)bx * ny + y) * kRowWords + lane * kTW, 512u, bar + slot);
+    } else if (lane < 18) {
+        const int i = lane - 9;
+        if (left)
+            bulk_g2s(dst + i * kStW, src + ((long long)(bx - 1) * ny + y) * kRowWords + i * kTW + (kTW - 4), 16u,
+                     bar + slot);
+    } else if (lane < 27) {
+        const int i = lane - 18;
+        if (right)
+            bulk_g2s(dst + i * kStW + 4 + kTW, src + ((long long)(bx + 1) * ny + y) * kRowWords + i * kTW, 16u,
+                     bar + slot);
+    }
+}
+
+// Pull of cell (x, y) from three staged rows (lattice rows y - 1, y, y + 1),
+// column c = 4 + lx within each direction's words; wall rules as pull_any.
+template <typename real, typename S, int PROB, bool FLOW>
+__device__ __forceinline__ void pull_staged(const SweepArgs<real> &a, const uint32_t *rm, const uint32_t *rc,
+                                            const uint32_t *rp, int c, int x, int y, bool interior,
+                                            real f[9], real g[9], double &q) {
+    uint32_t u[9];
+    if (interior) {  // no wall in reach (side-wall lanes are bounced afterwards)
+        u[0] = rc[0 * kStW + c];
+        u[1] = rc[1 * kStW + c - 1];
+        u[2] = rm[2 * kStW + c];
+        u[3] = rc[3 * kStW + c + 1];
+        u[4] = rp[4 * kStW + c];
+        u[5] = rm[5 * kStW + c - 1];
+        u[6] = rm[6 * kStW + c + 1];
+        u[7] = rp[7 * kStW + c + 1];
+        u[8] = rp[8 * kStW + c - 1];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (FLOW) f[i] = Store<S>::lo(u[i]);
+            g[i] = Store<S>::hi(u[i]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        const int sx = x - cx;
+        int sy = y - cy;
+        if (PROB == kStefan) sy = (sy < 0) ? sy + a.ny : ((sy >= a.ny) ? sy - a.ny : sy);
+        const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
+        const uint32_t *r = cy > 0 ? rm : (cy < 0 ? rp : rc);
+        const uint32_t w = in ? r[i * kStW + c - cx] : rc[opp_of(i) * kStW + c];
+        if (FLOW) f[i] = Store<S>::lo(w);
+        real gv = Store<S>::hi(w);
+        if (!in) {
+            bool heated;
+            if (PROB == kStefan) {
+                heated = sx < 0;
+            } else {
+                const int xc2 = 2 * x + 1 - cx;
+                heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
+            }
+            if (heated) {
+                const real wt = real(2) * w_of<real>(i) * real(Store<S>::kG);
+                q += (double)((wt - real(2) * gv) * (real(1) / real(Store<S>::kG)));
+                gv = wt - gv;
+            }
+        }
+        g[i] = gv;
+    }
+}
+
+template <typename real, typename S, int PROB, bool FLOW, int MODE>
+__global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
+    staged_kernel(const SweepArgs<real> a) {
+    static_assert(Store<S>::kDev, "the staged sweep reads the paired 16-bit layout");
+    extern __shared__ __align__(16) unsigned char st_smem[];
+    __shared__ double sh[32 * 4];
+    __shared__ int ok_sh;
+    uint32_t *rows = reinterpret_cast<uint32_t *>(st_smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(st_smem + (size_t)kStSlots * kStRow * 4);  // + 1 spare
+    pdl_launch_dependents();
+    const int lx = threadIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = blockIdx.x, band = blockIdx.y, nbands = gridDim.y;
+    const int y0 = (int)((long long)band * a.ny / nbands);
+    const int y1 = (int)((long long)(band + 1) * a.ny / nbands);
+    const int nb = y1 - y0;
+    const int dir = (band & 1) ? -1 : 1;
+    const int ys0 = (dir > 0 ? y0 : y1 - 1) - dir;  // staged row s: y = ys0 + s dir
+    if (threadIdx.x == 0) {
+        for (int k = 0; k <= kStSlots; ++k) mbar_init(bar + k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait();  // the previous step's populations
+    const uint32_t step_seed = step_prologue<real, S, MODE>(a, bx, band);
+    const int x = bx * kTW + lx;
+    const bool active = x < a.nx;
+    const int xw = bx * kTW + (lx & ~31);
+    const bool fastcol = xw >= 1 && xw + 31 <= a.nx - 2;
+    const int c = 4 + lx;
+
+    int issued = -1;  // last staged row issued (warp 0 keeps it)
+    if (warp == 0) {
+        const int n0 = min(kStSlots, nb + 2);
+        for (int s = 0; s < n0; ++s) stage_row<S, PROB>(a.src, a.nx, a.ny, a.ntx, bx, ys0, dir, s, rows, bar);
+        issued = n0 - 1;
+    }
+    CellSums<real> acc;
+    for (int p = 0; p < nb; ++p) {
+        if (p > 0) __syncthreads();  // every thread is done with staged row p - 1
+        if (warp == 0) {
+            const int s_new = p - 1 + kStSlots;
+            if (p > 0 && s_new <= nb + 1) {
+                stage_row<S, PROB>(a.src, a.nx, a.ny, a.ntx, bx, ys0, dir, s_new, rows, bar);
+                issued = s_new;
+            }
+            if (lane == 0) {
+                bool ok = true;
+                if (a.force_timeout && p == 0) ok = mbar_wait_bounded(bar + kStSlots, 0, a.wait_limit);
+                for (int s = (p == 0 ? 0 : p + 2); s <= p + 2 && ok; ++s)
+                    ok = mbar_wait_bounded(bar + s % kStSlots, (unsigned)(s / kStSlots) & 1u, a.wait_limit);
+                ok_sh = ok ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        if (!ok_sh) {
+            // a wait ran out: record it, let the copies in flight land, return
+            if (threadIdx.x == 0) {
+                a.rec->timeout = 1.0;
+                for (int s = (p == 0 ? 0 : p + 2); s <= issued; ++s)
+                    mbar_wait_bounded(bar + s % kStSlots, (unsigned)(s / kStSlots) & 1u, kStDrainLimit);
+            }
+            __syncthreads();
+            return;
+        }
+        // every thread observes the completed phases (immediate: thread 0 saw them)
+        for (int s = (p == 0 ? 0 : p + 2); s <= p + 2; ++s)
+            mbar_wait_bounded(bar + s % kStSlots, (unsigned)(s / kStSlots) & 1u, a.wait_limit);
+        if (!active) continue;
+        const int y = ys0 + (p + 1) * dir;
+        // staged rows of lattice rows y - 1 and y + 1 (s = p + 1 -+ dir)
+        const uint32_t *rc = rows + (size_t)((p + 1) % kStSlots) * kStRow;
+        const uint32_t *rlo = rows + (size_t)((dir > 0 ? p : p + 2) % kStSlots) * kStRow;
+        const uint32_t *rhi = rows + (size_t)((dir > 0 ? p + 2 : p) % kStSlots) * kStRow;
+        const bool rowok = PROB == kStefan || (y >= 1 && y <= a.ny - 2);
+        const bool wallfree = PROB == kCavity ? true : fastcol;  // Stefan: the left wall is heated
+        real f[9], g[9];
+        pull_staged<real, S, PROB, FLOW>(a, rlo, rc, rhi, c, x, y, rowok && wallfree, f, g, acc.q);
+        if (PROB == kCavity && rowok && !fastcol) {
+            // side-wall lanes: their wall directions bounce back (own cell)
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if ((cx_of(i) == 1 && x == 0) || (cx_of(i) == -1 && x == a.nx - 1)) {
+                    const uint32_t w = rc[opp_of(i) * kStW + c];
+                    if (FLOW) f[i] = Store<S>::lo(w);
+                    g[i] = Store<S>::hi(w);
+                }
+            }
+        }
+        finish_cell<real, S, FLOW, MODE>(a, x, y, cell_index<S>(x, y, 0, a.ny), f, g, step_seed, acc);
+    }
+    block_epilogue<real, PROB, MODE>(a, bx, band, gridDim.x, acc, sh);
 }
 
 // ---- batches: many lattices of one precision and problem kind per launch ----
@@ -899,7 +1276,7 @@ __global__ void __launch_bounds__(kReduceThreads)
     block_fold<4, A>(acc, kind, sh);
     if (threadIdx.x == 0) {
         DevRecord *rec = a.rec;
-        rec->step = rec->counter;
+        rec->step = (double)rec->counter;
         rec->melt_sum = dec_sum(acc[0]);
         rec->H_sum = dec_sum(acc[1]);
         rec->max_u = dec_max(acc[2]);
@@ -940,16 +1317,16 @@ __global__ void __launch_bounds__(kTW) init_kernel(const SweepArgs<real> a, doub
             const real H = (real)(amp * (2.0 * r - 1.0));
             real T, fl;
             invert(H, a.Lh, a.inv_Lh, T, fl);
-            const long long c = pop_index(x, y, 0, a.ny);
             // initial state: rounded to nearest
-            Store<S>::stg_rn(dst + c + 9 * kTW, H - T + w_of<real>(0) * T);
+            Store<S>::stg_rn(dst + cell_index<S>(x, y, 9, a.ny), H - T + w_of<real>(0) * T);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) Store<S>::stg_rn(dst + c + (9 + i) * kTW, w_of<real>(i) * T);
+            for (int i = 1; i < 9; ++i) Store<S>::stg_rn(dst + cell_index<S>(x, y, 9 + i, a.ny), w_of<real>(i) * T);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const real fi = w_of<real>(i) - f_ofs<real, S>(i);
-                Store<S>::stf_rn(dst + c + i * kTW, fi);
-                if (aux) Store<S>::stf_rn(aux + c + i * kTW, fi);
+                const long long c = cell_index<S>(x, y, i, a.ny);
+                Store<S>::stf_rn(dst + c, fi);
+                if (aux) Store<S>::stf_rn(aux + c, fi);
             }
             sfl += enc_sum(fl);
             sH += enc_sum(H);
@@ -968,15 +1345,14 @@ __global__ void __launch_bounds__(kTW) fields0_kernel(const SweepArgs<real> a) {
     const int y1 = min(y0 + a.rows, a.ny);
     if (x >= a.nx) return;
     for (int y = y0; y < y1; ++y) {
-        const long long c = pop_index(x, y, 0, a.ny);
         real g[9], H, rho = real(1);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = Store<S>::ldg(src + c + (9 + i) * kTW);
+        for (int i = 0; i < 9; ++i) g[i] = Store<S>::ldg(src + cell_index<S>(x, y, 9 + i, a.ny));
         H = sum9(g);
         if (FLOW) {
             real f[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = Store<S>::ldf(src + c + i * kTW) + f_ofs<real, S>(i);
+            for (int i = 0; i < 9; ++i) f[i] = Store<S>::ldf(src + cell_index<S>(x, y, i, a.ny)) + f_ofs<real, S>(i);
             rho = sum9(f);
         }
         real T, fl;
@@ -1001,13 +1377,13 @@ __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, in
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= nx) return;
-    const long long c = pop_index(x, y, 0, ny);
     const long long P = (long long)nx * ny, o = (long long)y * nx + x;
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         const bool isf = p < 9;
         const real ofs = isf ? f_ofs<real, S>(p) : real(0);
-        E *q = buf + c + p * kTW;
+        const long long c = cell_index<S>(x, y, p, ny);
+        E *q = buf + c;
         if (to_staging) {
             stage[p * P + o] = (double)((isf ? Store<S>::ldf(q) : Store<S>::ldg(q)) + ofs);
         } else {
@@ -1015,7 +1391,7 @@ __global__ void repack_kernel(void *bufv, void *buf2v, double *stage, int nx, in
             // caller data: stochastic codecs round it to nearest as well
             if (isf) {
                 Store<S>::stf_rn(q, v);
-                if (buf2) Store<S>::stf_rn(buf2 + c + p * kTW, v);
+                if (buf2) Store<S>::stf_rn(buf2 + c, v);
             } else {
                 Store<S>::stg_rn(q, v);
             }
@@ -1044,6 +1420,22 @@ static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cud
 template <typename real, typename S, int PROB, bool FLOW>
 static cudaError_t launch_mode(const SweepArgs<real> &a, int mode, dim3 grid, dim3 block,
                                cudaStream_t s, bool pdl) {
+    if constexpr (Store<S>::kDev) {
+        if (a.staged && (mode == kSweep || mode == kSweepDiag)) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = block;
+            cfg.dynamicSmemBytes = kStSmem;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = pdl ? 1 : 0;
+            return mode == kSweep ? cudaLaunchKernelEx(&cfg, staged_kernel<real, S, PROB, FLOW, kSweep>, a)
+                                  : cudaLaunchKernelEx(&cfg, staged_kernel<real, S, PROB, FLOW, kSweepDiag>, a);
+        }
+    }
     switch (mode) {
         case kSweep: return launch_k(lattice_kernel<real, S, PROB, FLOW, kSweep>, grid, block, s, pdl, a);
         case kSweepDiag:

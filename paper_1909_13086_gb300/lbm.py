@@ -68,7 +68,7 @@ class lbm_launch_stats(ctypes.Structure):
 
 
 EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_set_diag_every",
-            "lbm_set_launch", "lbm_get_launch_stats",
+            "lbm_set_launch", "lbm_get_launch_stats", "lbm_set_staging", "lbm_set_wait_limit",
             "lbm_read_fields", "lbm_diagnostics", "lbm_read_populations", "lbm_write_populations",
             "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
@@ -98,6 +98,8 @@ def lib() -> ctypes.CDLL:
     L.lbm_set_diag_every.argtypes = [H, ctypes.c_longlong]
     L.lbm_set_launch.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.lbm_get_launch_stats.argtypes = [H, ctypes.POINTER(lbm_launch_stats)]
+    L.lbm_set_staging.argtypes = [H, ctypes.c_int]
+    L.lbm_set_wait_limit.argtypes = [H, ctypes.c_longlong, ctypes.c_int]
     L.lbm_read_fields.argtypes = [H, ctypes.c_uint] + [_D] * 6
     L.lbm_diagnostics.argtypes = [H, ctypes.POINTER(lbm_diag)]
     L.lbm_read_populations.argtypes = [H, _D, _D, ctypes.POINTER(ctypes.c_longlong)]
@@ -180,6 +182,14 @@ def lbm_set_diag_every(h, k: int) -> None:
 
 def lbm_set_launch(h, rows: int = 1, prefetch: int = 4, graph_chunk: int = 128) -> None:
     _check(lib().lbm_set_launch(h, int(rows), int(prefetch), int(graph_chunk)), h)
+
+
+def lbm_set_staging(h, bands: int = -1) -> None:
+    _check(lib().lbm_set_staging(h, int(bands)), h)
+
+
+def lbm_set_wait_limit(h, tries: int = 1 << 20, force_timeout: bool = False) -> None:
+    _check(lib().lbm_set_wait_limit(h, int(tries), 1 if force_timeout else 0), h)
 
 
 def lbm_get_launch_stats(h) -> dict:

@@ -20,25 +20,39 @@ RS = PLANES * TW
 C = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
 
 
-def pop_index(x, y, p, ny):
-    return ((x // TW) * ny + y) * RS + p * TW + (x % TW)
+def plane_ofs(p, lx, paired):
+    """Element of plane p (0..8 f, 9..17 g) of column lx within a tile row:
+    planar for FP32 / FP64; for 16-bit storage (paired) f_i and g_i share the
+    32-bit word i * TW + lx, f in the low half (element 2 w), g in the high
+    half (element 2 w + 1)."""
+    return 2 * ((p % 9) * TW + lx) + (1 if p >= 9 else 0) if paired else p * TW + lx
 
 
-def load_offsets():
+def pop_index(x, y, p, ny, paired=False):
+    return ((x // TW) * ny + y) * RS + plane_ofs(p, x % TW, paired)
+
+
+def load_offsets(paired=False):
     """(base, offset) of the 18 loads: base 0 = own, 1 = left-shifted, 2 =
-    right-shifted; offset in elements relative to that base."""
+    right-shifted; offset in elements relative to that base.  Paired: word
+    offsets (row RS / 2 words, direction TW words) doubled, + 1 for g."""
     out = []
     for P in (0, 9):
         for i, (cx, cy) in enumerate(C):
             base = 1 if cx == 1 else (2 if cx == -1 else 0)
-            out.append((base, (P + i) * TW - cx - cy * RS, P + i, cx, cy))
+            if paired:
+                off = 2 * (i * TW - cx - cy * (RS // 2)) + (1 if P else 0)
+            else:
+                off = (P + i) * TW - cx - cy * RS
+            out.append((base, off, P + i, cx, cy))
     return out
 
 
-def check_width(nx, ny):
+def check_width(nx, ny, paired=False):
     ntx = (nx + TW - 1) // TW
     total = ntx * ny * RS
-    offs = load_offsets()
+    offs = load_offsets(paired)
+    cs = 2 if paired else 1
     for bx in range(ntx):
         for warp in range(TW // 32):
             xw = bx * TW + warp * 32
@@ -50,9 +64,9 @@ def check_width(nx, ny):
                 if x >= nx:
                     continue                # inactive lane
                 for y in range(1, ny - 1):  # interior rows only take the fast loads
-                    i0 = pop_index(x, y, 0, ny)
-                    iL = pop_index(x - 1, y, 0, ny) + 1 if (lx == 0 and x > 0) else i0
-                    iR = pop_index(x + 1, y, 0, ny) - 1 if (lx == TW - 1 and x < nx - 1) else i0
+                    i0 = pop_index(x, y, 0, ny, paired)
+                    iL = pop_index(x - 1, y, 0, ny, paired) + cs if (lx == 0 and x > 0) else i0
+                    iR = pop_index(x + 1, y, 0, ny, paired) - cs if (lx == TW - 1 and x < nx - 1) else i0
                     bases = (i0, iL, iR)
                     for base, off, plane, cx, cy in offs:
                         e = bases[base] + off
@@ -60,21 +74,38 @@ def check_width(nx, ny):
                         wall_lane = (cx == 1 and x == 0) or (cx == -1 and x == nx - 1)
                         if wall_lane:
                             # clamped: stays in the cell's own tile, rows y-1..y+1
-                            lo = pop_index(bx * TW, y - 1, 0, ny)
-                            hi = pop_index(bx * TW, y + 1, 0, ny) + RS
+                            lo = pop_index(bx * TW, y - 1, 0, ny, paired)
+                            hi = pop_index(bx * TW, y + 1, 0, ny, paired) + RS
                             assert lo <= e < hi, (nx, ny, x, y, plane)
                             assert sidewall
                         else:
                             # a true neighbour: the source cell's own plane element
-                            want = pop_index(x - cx, y - cy, plane, ny)
+                            want = pop_index(x - cx, y - cy, plane, ny, paired)
                             assert e == want, (nx, ny, x, y, plane)
+                            if paired and plane < 9:  # the 32-bit word is aligned
+                                assert e % 2 == 0
 
 
+@pytest.mark.parametrize("paired", [False, True])
 @pytest.mark.parametrize("nx", [2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 300, 383, 384])
-def test_fast_loads_stay_in_the_buffer(nx):
-    check_width(nx, 5)
+def test_fast_loads_stay_in_the_buffer(nx, paired):
+    check_width(nx, 5, paired)
 
 
-def test_fast_loads_for_every_width_up_to_four_tiles():
+@pytest.mark.parametrize("paired", [False, True])
+def test_fast_loads_for_every_width_up_to_four_tiles(paired):
     for nx in range(2, 4 * TW + 2):
-        check_width(nx, 3)
+        check_width(nx, 3, paired)
+
+
+def test_paired_layout_is_a_permutation_of_the_tile_row():
+    """Both layouts place the 18 planes of a tile row's 128 cells on the same
+    18 * 128 elements, each exactly once, and a (g_i, f_i) word starts on an
+    even element."""
+    for paired in (False, True):
+        seen = sorted(plane_ofs(p, lx, paired) for p in range(PLANES) for lx in range(TW))
+        assert seen == list(range(RS))
+    for i in range(9):
+        for lx in range(TW):
+            f, g = plane_ofs(i, lx, True), plane_ofs(9 + i, lx, True)
+            assert f % 2 == 0 and g == f + 1
