@@ -519,6 +519,8 @@ def run_batch(args) -> None:
     b = lbm.Batch(n, stream.cuda_stream)
     for lat in lats:
         b.add(lat)
+    # launch shape picked by the batch autotuner (scratch lattices, untimed)
+    tuned = lbm.lbm_batch_autotune(b.b, 50) if not args.no_autotune else None
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clocks:
         b.step(args.warmup)
@@ -546,7 +548,10 @@ def run_batch(args) -> None:
                    # both population buffers together are the algorithmic bytes of a step
                    "l2": (f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB of populations), no flush"
                           if alg_bytes > 129e6 else
-                          f"inputs fit in L2 ({alg_bytes / 1e6:.0f} MB of populations)")},
+                          f"inputs fit in L2 ({alg_bytes / 1e6:.0f} MB of populations)"),
+                   "launch": ({"rows": tuned["rows"], "prefetch": tuned["prefetch"],
+                               "interleave": tuned["interleave"], "by": "lbm_batch_autotune"}
+                              if tuned else "default")},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": profiled_traffic(prec, n),
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
@@ -571,6 +576,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-autotune", action="store_true", help="--batch: keep the default launch shape")
     ap.add_argument("--batch", type=int, default=0,
                     help=f"time a batch of this many {BATCH_NX}x{BATCH_NY} cavities instead")
     args = ap.parse_args(argv)

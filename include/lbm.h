@@ -272,7 +272,7 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
  * step) and, as lbm_step does, replays a piece from a CUDA graph from the
  * second time it is asked for (graphs are kept per batch composition); every
  * launch uses programmatic stream serialization.  The batch uses its own
- * launch shape (2 rows per block, 4 with 16-bit storage), whatever the
+ * launch shape (lbm_batch_set_launch, lbm_batch_autotune), whatever the
  * members' lbm_set_launch settings.  Each
  * step of a member computes exactly what lbm_step would: the populations are
  * bitwise those of stepping it alone, and so are the diagnostics except on
@@ -306,6 +306,30 @@ int lbm_batch_count(lbm_batch b, int *count);
 
 /* Advance every member n >= 0 steps, asynchronously on the batch's stream. */
 int lbm_batch_step(lbm_batch b, long long n);
+
+/* Launch shape of the batch's step kernel: rows of a member walked by each
+ * block (0 = the default: 1, or 4 with 16-bit storage; up to 1024), the L2
+ * prefetch distance in rows (-1 = the default: 4, or 8 with 16-bit storage),
+ * and interleave = 1 (the default) to number the blocks of a one-size batch
+ * member after member (block b belongs to member b mod n) instead of member
+ * by member (0; a batch whose members' block counts differ is always member
+ * by member).  Results do not depend on it.  Takes effect at the next
+ * lbm_batch_step.  Errors: LBM_ERR_ARG. */
+int lbm_batch_set_launch(lbm_batch b, int rows_per_block, int prefetch_rows, int interleave);
+
+/* Autotuner for a batch: times rows per block (1, 2, 4) x prefetch distance
+ * (0, 4, 16 rows; 0, 8, 24 with 16-bit storage) x block order (member by
+ * member, interleaved) for steps_per_trial steps each (best of three, after a
+ * warm-up) on scratch lattices of the batch's composition -- the same sizes,
+ * precision and parameters, allocated and freed here; the members' states are
+ * not touched -- and applies the fastest with lbm_batch_set_launch.  The
+ * choice is cached per composition (precision, problem, flow and the members'
+ * sizes in order) for the life of the process.  Outputs (may be NULL): the
+ * chosen shape and its time per step in microseconds (0 when it came from the
+ * cache).  Synchronises.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (empty batch),
+ * LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_batch_autotune(lbm_batch b, int steps_per_trial, int *rows, int *prefetch, int *interleave,
+                       float *us_per_step);
 
 /* Free the batch (not its members). */
 int lbm_batch_destroy(lbm_batch b);

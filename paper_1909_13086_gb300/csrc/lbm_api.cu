@@ -17,6 +17,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "lbm.h"
@@ -923,6 +924,9 @@ struct lbm_batch_s {
     std::vector<int> host_parity;
     int nblocks = 0;
     int uniform = 0;          // blocks per member when all members have the same count
+    int rows = 0;             // launch shape: rows per block (0: 1, or 4 with 16-bit storage),
+    int prefetch = -1;        // L2 prefetch distance (-1: 4 rows, 8 with 16-bit storage),
+    int interleave = 1;       // interleaved block order (uniform batches only; see batch_kernel)
     bool dirty = true;        // table must be rebuilt and uploaded
     int precision = -1, problem = -1, flow = -1;
     int graph_chunk = 128;    // longest graph-replayed piece; even, so that every
@@ -967,13 +971,13 @@ void batch_drop_graph(lbm_batch_s *b) {
 template <typename real>
 size_t entry_bytes() { return sizeof(BatchEntry<real>); }
 
-// Launch shape of a batch: each block walks kBatchRows rows of its lattice
-// (4 with 16-bit storage, else 2), whatever the members' own lbm_set_launch
-// settings.  A batch block first reads its lattice's table entry (two
-// dependent reads), so more rows per block amortise that start-up; on GB300,
-// 64 cavities of 256 x 128: FP32 62.8 -> 57.4 us per step with 2 rows,
-// BF16-SR 59.3 -> 47.3 us with 4.  Results do not depend on it.
-constexpr int kBatchRows32 = 2, kBatchRows16 = 4, kBatchPrefetch = 4;
+// Default launch shape of a batch, whatever the members' own lbm_set_launch
+// settings: 1 row per block (4 with 16-bit storage), L2 prefetch 4 rows ahead
+// (8), blocks of a one-size batch interleaved over the members -- what
+// lbm_batch_autotune picks for 64 cavities of 256 x 128 on GB300 (FP32 54.5 ->
+// 47.0 us per step against 2 rows member by member; BF16-SR 43.3 -> 39.5 us).
+// Results do not depend on it.
+constexpr int kBatchRows32 = 1, kBatchRows16 = 4, kBatchPrefetch32 = 4, kBatchPrefetch16 = 8;
 
 template <typename real>
 void batch_build(lbm_batch_s *b) {
@@ -984,14 +988,14 @@ void batch_build(lbm_batch_s *b) {
     int start = 0;
     for (size_t r = 0; r < b->members.size(); ++r) {
         lbm_s *h = b->members[r];
-        const int rows = h->esize == 2 ? kBatchRows16 : kBatchRows32;
+        const int rows = b->rows > 0 ? b->rows : (h->esize == 2 ? kBatchRows16 : kBatchRows32);
         const int gy = (h->ny + rows - 1) / rows;
         BatchEntry<real> e{};
         for (int p = 0; p < 2; ++p) {
             e.a[p] = make_args<real>(h, h->buf[p], h->buf[p ^ 1]);
             e.a[p].parity = p;
             e.a[p].rows = rows;
-            e.a[p].prefetch = kBatchPrefetch;
+            e.a[p].prefetch = b->prefetch >= 0 ? b->prefetch : (h->esize == 2 ? kBatchPrefetch16 : kBatchPrefetch32);
             e.a[p].nq = h->p.problem == LBM_CAVITY ? (int)h->grid.x : gy;
         }
         e.start = start;
@@ -1035,7 +1039,8 @@ int batch_steps(lbm_batch_s *b, long long n) {
     auto direct = [&](long long from, long long len, bool diag) -> int {
         for (long long j = 0; j < len; ++j) {
             const cudaError_t e = launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->uniform,
-                                                        b->nblocks, b->problem, b->flow != 0,
+                                                        b->uniform > 0 ? b->interleave : 0, b->nblocks,
+                                                        b->problem, b->flow != 0,
                                                         diag && j == len - 1, (int)((from + j) & 1),
                                                         b->stream, true);
             if (e != cudaSuccess) return batch_err(LBM_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
@@ -1217,6 +1222,17 @@ int lbm_batch_step(lbm_batch b, long long n) {
     return LBM_OK;
 }
 
+int lbm_batch_set_launch(lbm_batch b, int rows_per_block, int prefetch_rows, int interleave) {
+    if (!b || rows_per_block < 0 || rows_per_block > 1024 || prefetch_rows < -1 || (interleave != 0 && interleave != 1))
+        return batch_err(LBM_ERR_ARG,
+                         "lbm_batch_set_launch: rows in [0, 1024], prefetch_rows >= -1, interleave 0 or 1");
+    b->rows = rows_per_block;
+    b->prefetch = prefetch_rows;
+    b->interleave = interleave;
+    b->dirty = true;
+    return LBM_OK;
+}
+
 int lbm_batch_destroy(lbm_batch b) {
     if (!b) return LBM_OK;
     DeviceGuard g(b->device);
@@ -1230,6 +1246,117 @@ int lbm_batch_destroy(lbm_batch b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch autotuner: times launch shapes of a batch (rows per block, L2
+// prefetch distance, interleaved block order) on scratch lattices of the same
+// composition and applies the fastest; cached per composition for the
+// process.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchTune {
+    std::string key;
+    int rows, prefetch, interleave;
+    float us_per_step;
+};
+std::mutex g_btune_mutex;
+std::vector<BatchTune> g_btune_cache;
+
+// The composition: precision, problem, flow, then every member's size in order.
+std::string batch_key(const lbm_batch_s *b) {
+    std::string k = std::to_string(b->precision) + "/" + std::to_string(b->problem) + "/" +
+                    std::to_string(b->flow);
+    for (const lbm_s *h : b->members) k += "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny);
+    return k;
+}
+
+}  // namespace
+
+extern "C" int lbm_batch_autotune(lbm_batch b, int steps_per_trial, int *rows_out, int *prefetch_out,
+                                  int *interleave_out, float *us_per_step_out) {
+    if (!b || steps_per_trial < 1) return batch_err(LBM_ERR_ARG, "lbm_batch_autotune: bad argument");
+    if (b->members.empty()) return batch_err(LBM_ERR_STATE, "lbm_batch_autotune: the batch is empty");
+    const std::string key = batch_key(b);
+    BatchTune best{key, b->rows, b->prefetch, b->interleave, 0.0f};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_btune_mutex);
+        for (const BatchTune &e : g_btune_cache)
+            if (e.key == key) {
+                best = e;
+                cached = true;
+            }
+    }
+    if (!cached) {
+        DeviceGuard g(b->device);
+        // scratch lattices of the same sizes and parameters, in a scratch batch
+        // on the batch's stream: the members' states are not touched
+        std::vector<lbm_handle> scratch;
+        lbm_batch t = nullptr;
+        int rc = lbm_batch_create((int)b->members.size(), b->stream, &t);
+        for (size_t r = 0; r < b->members.size() && rc == LBM_OK; ++r) {
+            const lbm_s *h = b->members[r];
+            lbm_handle s = nullptr;
+            rc = lbm_create(h->nx, h->ny, h->precision, b->stream, &s);
+            if (rc == LBM_OK) {
+                scratch.push_back(s);
+                rc = lbm_set_params(s, &h->p);
+            }
+            if (rc == LBM_OK) rc = lbm_batch_add(t, s);
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+            rc = LBM_ERR_CUDA;
+        const bool sixteen = b->members[0]->esize == 2;
+        const int rows_c[] = {1, 2, 4};
+        const int pf32[] = {0, 4, 16}, pf16[] = {0, 8, 24};
+        const int *pf_c = sixteen ? pf16 : pf32;
+        const int ninter = b->members.size() > 1 ? 2 : 1;  // interleaving needs several members
+        best.us_per_step = 1e30f;
+        for (int rows : rows_c) {
+            for (int k = 0; k < 3 && rc == LBM_OK; ++k) {
+                for (int il = 0; il < ninter && rc == LBM_OK; ++il) {
+                    rc = lbm_batch_set_launch(t, rows, pf_c[k], il);
+                    if (rc == LBM_OK) rc = lbm_batch_step(t, 4);  // warm-up, table upload
+                    if (rc == LBM_OK && il == 1 && t->uniform == 0) break;  // not a one-size batch
+                    float best_ms = 1e30f;
+                    for (int rep = 0; rep < 3 && rc == LBM_OK; ++rep) {  // the second replays a graph
+                        if (cudaEventRecord(e0, t->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+                        if (rc == LBM_OK) rc = lbm_batch_step(t, steps_per_trial);
+                        if (rc == LBM_OK && (cudaEventRecord(e1, t->stream) != cudaSuccess ||
+                                             cudaEventSynchronize(e1) != cudaSuccess))
+                            rc = LBM_ERR_CUDA;
+                        float ms = 0.0f;
+                        if (rc == LBM_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms)
+                            best_ms = ms;
+                    }
+                    const float us = best_ms * 1000.0f / (float)steps_per_trial;
+                    if (rc == LBM_OK && us < best.us_per_step) {
+                        best.rows = rows;
+                        best.prefetch = pf_c[k];
+                        best.interleave = il;
+                        best.us_per_step = us;
+                    }
+                }
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (t) lbm_batch_destroy(t);
+        for (lbm_handle s : scratch) lbm_destroy(s);
+        if (rc != LBM_OK) return batch_err(rc < 0 ? rc : LBM_ERR_CUDA, "lbm_batch_autotune: trial failed");
+        std::lock_guard<std::mutex> lock(g_btune_mutex);
+        g_btune_cache.push_back(best);
+    }
+    const int rc = lbm_batch_set_launch(b, best.rows, best.prefetch, best.interleave);
+    if (rc != LBM_OK) return rc;
+    if (rows_out) *rows_out = best.rows;
+    if (prefetch_out) *prefetch_out = best.prefetch;
+    if (interleave_out) *interleave_out = best.interleave;
+    if (us_per_step_out) *us_per_step_out = cached ? 0.0f : best.us_per_step;
+    return LBM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // lbm_step_static: one diagnostic sweep on caller-owned buffers, with no

@@ -1207,7 +1207,10 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
 // blocks an SM runs), then the whole entry, copied into shared memory 16 bytes
 // per thread, alongside the parity word.  When every entry has the same number
 // of blocks (`uniform`; a serving group's lattices share one size) the entry
-// is blockIdx.x / uniform and the search and its barrier are skipped.
+// is blockIdx.x / uniform and the search and its barrier are skipped; with
+// `interleave` set (uniform batches only) consecutive blocks belong to
+// consecutive entries instead -- entry b mod n, local block b / n -- so that
+// the blocks resident at one time spread over all the lattices.
 __device__ __forceinline__ int batch_find(const int *starts, int n, int b) {
     int lo = 0, hi = n - 1;  // last entry with starts[r] <= b
     while (lo < hi) {
@@ -1220,7 +1223,7 @@ __device__ __forceinline__ int batch_find(const int *starts, int n, int b) {
 template <typename real, typename S, int PROB, bool FLOW, int MODE>
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     batch_kernel(const BatchEntry<real> *entries, const int *starts, const int *parity, int n,
-                 int uniform, int j) {
+                 int uniform, int interleave, int j) {
     static_assert(sizeof(BatchEntry<real>) % 16 == 0, "entries are copied in 16-byte pieces");
     __shared__ double sh[32 * 4];
     __shared__ __align__(16) unsigned char entry_sh[sizeof(BatchEntry<real>)];
@@ -1232,7 +1235,7 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     // that step only before touching the populations.
     int r;
     if (uniform > 0) {
-        r = (int)(blockIdx.x / (unsigned)uniform);
+        r = interleave ? (int)(blockIdx.x % (unsigned)n) : (int)(blockIdx.x / (unsigned)uniform);
     } else {
         if (threadIdx.x == 0) meta[0] = batch_find(starts, n, blockIdx.x);
         __syncthreads();
@@ -1246,7 +1249,7 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     __syncthreads();
     pdl_wait();
     const BatchEntry<real> &e = *reinterpret_cast<const BatchEntry<real> *>(entry_sh);
-    const int l = blockIdx.x - e.start;
+    const int l = (uniform > 0 && interleave) ? (int)(blockIdx.x / (unsigned)n) : (int)blockIdx.x - e.start;
     sweep_block<real, S, PROB, FLOW, MODE>(e.a[meta[1]], l % e.gx, l / e.gx, e.gx, sh);
 }
 
@@ -1474,16 +1477,16 @@ cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int
 
 template <typename real, typename S>
 cudaError_t launch_batch(const void *entries, const int *starts, const int *parity, int n,
-                         int uniform, int nblocks, int problem, bool flow, bool diag, int j,
-                         cudaStream_t s, bool pdl) {
+                         int uniform, int interleave, int nblocks, int problem, bool flow, bool diag,
+                         int j, cudaStream_t s, bool pdl) {
     const BatchEntry<real> *e = static_cast<const BatchEntry<real> *>(entries);
     const dim3 grid(nblocks), block(kTW);
     cudaError_t err;
 #define BTRIRT_BATCH(PROB, FLOW)                                                                   \
     err = diag ? launch_k(batch_kernel<real, S, PROB, FLOW, kSweepDiag>, grid, block, s, pdl, e,   \
-                          starts, parity, n, uniform, j)                                           \
+                          starts, parity, n, uniform, interleave, j)                               \
                : launch_k(batch_kernel<real, S, PROB, FLOW, kSweep>, grid, block, s, pdl, e, starts, \
-                          parity, n, uniform, j);
+                          parity, n, uniform, interleave, j);
     if (problem == kCavity) {
         if (flow) { BTRIRT_BATCH(kCavity, true) } else { BTRIRT_BATCH(kCavity, false) }
     } else {
@@ -1533,6 +1536,6 @@ cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, 
                                                  cudaStream_t);                                  \
     template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t); \
     template cudaError_t launch_batch<REAL, S>(const void *, const int *, const int *, int, int,  \
-                                               int, int, bool, bool, int, cudaStream_t, bool);
+                                               int, int, int, bool, bool, int, cudaStream_t, bool);
 
 }  // namespace btrirt

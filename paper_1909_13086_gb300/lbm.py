@@ -73,7 +73,7 @@ EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_
             "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
             "lbm_batch_step", "lbm_batch_destroy", "lbm_autotune", "lbm_set_history",
-            "lbm_read_history")
+            "lbm_read_history", "lbm_batch_set_launch", "lbm_batch_autotune")
 
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
@@ -120,6 +120,10 @@ def lib() -> ctypes.CDLL:
     L.lbm_batch_count.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
     L.lbm_batch_step.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
     L.lbm_batch_destroy.argtypes = [ctypes.c_void_p]
+    L.lbm_batch_set_launch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_float)]
     L.lbm_step_static.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(lbm_params), ctypes.c_longlong,
                                   ctypes.c_void_p, ctypes.POINTER(lbm_diag)]
@@ -277,6 +281,17 @@ def lbm_batch_count(b) -> int:
 
 def lbm_batch_step(b, n: int) -> None:
     _check(lib().lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_set_launch(b, rows: int = 0, prefetch: int = -1, interleave: int = 0) -> None:
+    _check(lib().lbm_batch_set_launch(b, int(rows), int(prefetch), int(interleave)))
+
+
+def lbm_batch_autotune(b, steps_per_trial: int = 50) -> dict:
+    rows, pf, il, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().lbm_batch_autotune(b, int(steps_per_trial), ctypes.byref(rows), ctypes.byref(pf),
+                                    ctypes.byref(il), ctypes.byref(us)))
+    return {"rows": rows.value, "prefetch": pf.value, "interleave": il.value, "us_per_step": us.value}
 
 
 def lbm_batch_destroy(b) -> None:

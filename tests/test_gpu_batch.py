@@ -213,3 +213,51 @@ def test_batch_member_matches_oracle(orc, stream, prec):
         d, dr = members[k].diagnostics(), ref.diagnostics()
         assert d["step"] == steps
         assert d["Q_cum"] == pytest.approx(dr["Q_cum"], rel=1e-5 if prec == "fp32" else 1e-12)
+
+
+@pytest.mark.parametrize("rows,prefetch,interleave", [(1, 0, 1), (4, 16, 1), (1, 4, 0), (3, 8, 0)])
+def test_batch_launch_shapes_equal_solo(stream, rows, prefetch, interleave):
+    """Rows per block, prefetch distance and the interleaved block order of a
+    one-size batch change no result: members end bitwise where solo runs do,
+    diagnostics included (FP32 sums are exact fixed-point sums)."""
+    cases = [(256, 128, dict(Ra=1e6, strip_center=c, seed=k)) for k, c in enumerate((0.2, 0.5, 0.8))]
+    solo = [make(stream, "fp32", nx, ny, kw) for nx, ny, kw in cases]
+    for lat in solo:
+        lat.step(130)
+    members = [make(stream, "fp32", nx, ny, kw) for nx, ny, kw in cases]
+    b = lbm.Batch(4, stream)
+    for lat in members:
+        b.add(lat)
+    lbm.lbm_batch_set_launch(b.b, rows, prefetch, interleave)
+    b.step(130)
+    for s, m in zip(solo, members):
+        assert_same(state(s), state(m))
+
+
+def test_batch_autotune_leaves_state_and_caches(stream):
+    cases = [(256, 128, dict(Ra=1e6, strip_center=0.35)), (300, 77, dict(Ra=1e5)),
+             (256, 128, dict(Ra=1e7, strip_center=0.65))]
+    members = [make(stream, "fp32", nx, ny, kw) for nx, ny, kw in cases]
+    b = lbm.Batch(4, stream)
+    for lat in members:
+        b.add(lat)
+    b.step(10)
+    before = [state(m) for m in members]
+    t1 = lbm.lbm_batch_autotune(b.b, 30)
+    assert t1["rows"] in (1, 2, 4) and t1["prefetch"] in (0, 4, 16) and t1["interleave"] == 0
+    assert t1["us_per_step"] > 0
+    for s0, m in zip(before, members):
+        assert_same(s0, state(m))                     # the members' states are untouched
+    other = [make(stream, "fp32", nx, ny, kw) for nx, ny, kw in cases]
+    b2 = lbm.Batch(4, stream)
+    for lat in other:
+        b2.add(lat)
+    t2 = lbm.lbm_batch_autotune(b2.b, 30)              # same composition: from the cache
+    assert t2["us_per_step"] == 0.0
+    assert (t2["rows"], t2["prefetch"], t2["interleave"]) == (t1["rows"], t1["prefetch"], t1["interleave"])
+    b.step(90)
+    solo = [make(stream, "fp32", nx, ny, kw) for nx, ny, kw in cases]
+    for lat in solo:
+        lat.step(100)
+    for s, m in zip(solo, members):
+        assert_same(state(s), state(m))
