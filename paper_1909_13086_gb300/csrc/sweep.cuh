@@ -612,13 +612,15 @@ __device__ __forceinline__ void block_fold(T (&v)[NV], const int (&kind)[NV], vo
 
 // ---- diagnostics accumulators ----
 // FP64 path: FP64 throughout.  FP32 path: each cell's f_l and H are encoded as
-// 64-bit fixed point (2^-24 units) and every sum from there on is an exact
-// integer sum -- independent of the order, so of the launch shape and of
-// batching, and on the integer pipes: on GB300 the FP64 rate (~2
-// FMA/clock/SM) makes FP64 shuffle folds cost as much as the sweep itself.
-// The maximum |u| travels as the bit pattern of a non-negative float (integer
-// order = float order).  The record receives FP64 values decoded once at the
-// end.  Range: totals up to 2^39 (5.5e11) per quantity.
+// fixed point (2^-24 units, rounded to nearest once per cell) and every sum
+// from there on is an exact integer sum -- independent of the order, so of
+// the launch shape and of batching, and on the integer pipes: on GB300 the
+// FP64 rate (~2 FMA/clock/SM) makes FP64 shuffle folds cost as much as the
+// sweep itself.  In the sweeps each row of a warp is summed at once by the
+// warp-reduction unit in 32-bit integers (see diag_row).  The maximum |u|
+// travels as the bit pattern of a non-negative float (integer order = float
+// order).  The record receives FP64 values decoded once at the end.  Range:
+// |H| < 2^31 per cell, totals up to 2^39 (5.5e11) per quantity.
 template <typename real>
 struct DiagAcc {
     using T = double;
@@ -640,8 +642,9 @@ __device__ __forceinline__ double dec_max(double v) { return v; }
 // Per-block diagnostics partials.  A sweep (or the init kernel) writes one
 // record of 4 accumulators per block with plain stores -- no fence, no ticket,
 // so a block's lifetime does not grow -- and diag_reduce_kernel, launched
-// right after on the same stream, folds them into the FP64 record.  Inputs are
-// the thread's sums of enc_sum(f_l) and enc_sum(H) over its cells.
+// right after on the same stream, folds them into the FP64 record.  Inputs
+// here are the thread's sums of enc_sum(f_l) and enc_sum(H) over its cells
+// (the init kernel, and the FP64 sweeps).
 template <typename real>
 __device__ __forceinline__ void diag_partial(typename DiagAcc<real>::T sfl,
                                              typename DiagAcc<real>::T sH, real umax2, bool bad,
@@ -778,7 +781,9 @@ __device__ __forceinline__ uint32_t step_prologue(const SweepArgs<real> &a, int 
 // Diagnostics accumulators of one thread.
 // The heated-wall inflow is summed in FP64 from the first crossing on: a sum
 // of a band's working-precision terms is then exact, so the flux does not
-// depend on how many rows a block covers.
+// depend on how many rows a block covers.  sfl and sH: the thread's sums
+// (FP64 sweeps), or the warp's sums over its rows so far, held by every lane
+// (FP32 sweeps, see diag_row).
 template <typename real>
 struct CellSums {
     double q = 0.0;
@@ -787,12 +792,85 @@ struct CellSums {
     bool bad = false;
 };
 
+// The diagnostics of one cell; zero for a lane without a cell.
+template <typename real>
+struct CellDiag {
+    real fl = real(0), H = real(0), u2 = real(0);
+    bool bad = false;
+};
+
+// One row of a warp into the accumulators; every lane of the warp calls it.
+// FP32: f_l (at most 2^24 in fixed point) and H -- split into its integer part
+// and its fraction, both exact in a float, so that each partial fits in 32
+// bits -- are summed over the row's 32 cells by the warp-reduction unit, and
+// the totals widened to 64 bits: the same exact sum of the cells' rounded
+// values that encoding every cell in 64 bits gives (trunc(H) is an integer, so
+// rounding H 2^24 to nearest equals trunc(H) 2^24 + rounding its fraction),
+// for a handful of instructions per cell instead of a 64-bit conversion on
+// the FP64 pipe and a 64-bit shuffle tree per block.
+__device__ __forceinline__ void diag_row(CellSums<float> &acc, const CellDiag<float> &c) {
+    const unsigned full = 0xffffffffu;
+    const int fl = __float2int_rn(c.fl * kFixScale);
+    const float hi = truncf(c.H);
+    const int h_hi = (int)hi;
+    const int h_lo = __float2int_rn((c.H - hi) * kFixScale);
+    acc.sfl += (long long)__reduce_add_sync(full, fl);
+    acc.sH += ((long long)__reduce_add_sync(full, h_hi) << 24) + (long long)__reduce_add_sync(full, h_lo);
+    acc.umax2 = fmaxf(acc.umax2, c.u2);
+    acc.bad |= c.bad;
+}
+__device__ __forceinline__ void diag_row(CellSums<double> &acc, const CellDiag<double> &c) {
+    acc.sfl += c.fl;
+    acc.sH += c.H;
+    acc.umax2 = max(acc.umax2, c.u2);
+    acc.bad |= c.bad;
+}
+
+// The block's partial from the accumulators of diag_row.  FP32: lane 0 of
+// each warp holds the warp's sums; the warps meet in shared memory and thread
+// 0 adds them in warp order.  FP64: the thread sums go through diag_partial.
+__device__ __forceinline__ void diag_partial_rows(const CellSums<float> &acc, double *dpart, size_t bid,
+                                                  double *shv) {
+    const unsigned full = 0xffffffffu;
+    // non-negative floats compare as their bit patterns
+    const unsigned um = __reduce_max_sync(full, __float_as_uint(acc.umax2));
+    const int wbad = __any_sync(full, acc.bad) ? 1 : 0;
+    long long *sh = reinterpret_cast<long long *>(shv);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[4 * warp + 0] = acc.sfl;
+        sh[4 * warp + 1] = acc.sH;
+        sh[4 * warp + 2] = (long long)um;
+        sh[4 * warp + 3] = wbad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long v[4] = {0, 0, 0, 0};
+        const int nwarps = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nwarps; ++w) {
+            v[0] += sh[4 * w + 0];
+            v[1] += sh[4 * w + 1];
+            v[2] = max(v[2], sh[4 * w + 2]);
+            v[3] = max(v[3], sh[4 * w + 3]);
+        }
+        long long *d = reinterpret_cast<long long *>(dpart) + 4 * bid;
+        d[0] = v[0];
+        d[1] = v[1];
+        d[2] = enc_max(sqrtf(__uint_as_float((unsigned)v[2])));
+        d[3] = v[3];
+    }
+}
+__device__ __forceinline__ void diag_partial_rows(const CellSums<double> &acc, double *dpart, size_t bid,
+                                                  double *sh) {
+    diag_partial<double>(acc.sfl, acc.sH, acc.umax2, acc.bad, dpart, bid, sh);
+}
+
 // Collide the pulled populations of cell (x, y) and store them at element
 // offset c (cell_index(x, y, 0)) of the destination (MODE == kFields: write
 // the fields instead).
 template <typename real, typename S, bool FLOW, int MODE>
 __device__ __forceinline__ void finish_cell(const SweepArgs<real> &a, int x, int y, long long c, real f[9],
-                                            real g[9], uint32_t step_seed, CellSums<real> &acc) {
+                                            real g[9], uint32_t step_seed, CellDiag<real> &cd) {
     using E = typename Store<S>::elem;
     if (MODE == kFields) {
         const Macro<real> m = cell_update<real, S, FLOW, false>(a, f, g);
@@ -833,10 +911,10 @@ __device__ __forceinline__ void finish_cell(const SweepArgs<real> &a, int x, int
         }
     }
     if (MODE == kSweepDiag) {
-        acc.sfl += enc_sum(m.fl);
-        acc.sH += enc_sum(m.H);
-        acc.umax2 = max(acc.umax2, m.ux * m.ux + m.uy * m.uy);
-        acc.bad |= !(isfinite(m.H) && isfinite(m.rho));
+        cd.fl = m.fl;
+        cd.H = m.H;
+        cd.u2 = m.ux * m.ux + m.uy * m.uy;
+        cd.bad = !(isfinite(m.H) && isfinite(m.rho));
     }
 }
 
@@ -883,8 +961,7 @@ __device__ __forceinline__ void block_epilogue(const SweepArgs<real> &a, int bx,
     }
     // ---- diagnostics: sums within the warp in the working precision (32
     // threads x their cells), then FP64 across warps and blocks ----
-    if (MODE == kSweepDiag)
-        diag_partial<real>(acc.sfl, acc.sH, acc.umax2, acc.bad, a.dpart, (size_t)bx + (size_t)by * gx, sh);
+    if (MODE == kSweepDiag) diag_partial_rows(acc, a.dpart, (size_t)bx + (size_t)by * gx, sh);
 }
 
 // One block's work: the tile column bx (kTW cells) and the row band by
@@ -925,15 +1002,18 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
 
     CellSums<real> acc;
     for (int y = y0; y < y1; ++y, i0 += kRS, iL += kRS, iR += kRS) {
-        if (!active) continue;
-        real f[9], g[9];
-        if ((fastcol || sidewall) && y >= 1 && y <= a.ny - 2) {
-            pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
-            if (sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
-        } else {
-            pull_any<real, S, PROB, FLOW>(a, x, y, f, g, acc.q);
+        CellDiag<real> cd;
+        if (active) {
+            real f[9], g[9];
+            if ((fastcol || sidewall) && y >= 1 && y <= a.ny - 2) {
+                pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
+                if (sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
+            } else {
+                pull_any<real, S, PROB, FLOW>(a, x, y, f, g, acc.q);
+            }
+            finish_cell<real, S, FLOW, MODE>(a, x, y, i0, f, g, step_seed, cd);
         }
-        finish_cell<real, S, FLOW, MODE>(a, x, y, i0, f, g, step_seed, acc);
+        if (MODE == kSweepDiag) diag_row(acc, cd);  // the whole warp, active or not
     }
     block_epilogue<real, PROB, MODE>(a, bx, by, gx, acc, sh);
 }
@@ -1171,7 +1251,11 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
         // every thread observes the completed phases (immediate: thread 0 saw them)
         for (int s = (p == 0 ? 0 : p + 2); s <= p + 2; ++s)
             mbar_wait_bounded(bar + s % kStSlots, (unsigned)(s / kStSlots) & 1u, a.wait_limit);
-        if (!active) continue;
+        CellDiag<real> cd;
+        if (!active) {
+            if (MODE == kSweepDiag) diag_row(acc, cd);
+            continue;
+        }
         const int y = ys0 + (p + 1) * dir;
         // staged rows of lattice rows y - 1 and y + 1 (s = p + 1 -+ dir)
         const uint32_t *rc = rows + (size_t)((p + 1) % kStSlots) * kStRow;
@@ -1192,7 +1276,8 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
                 }
             }
         }
-        finish_cell<real, S, FLOW, MODE>(a, x, y, cell_index<S>(x, y, 0, a.ny), f, g, step_seed, acc);
+        finish_cell<real, S, FLOW, MODE>(a, x, y, cell_index<S>(x, y, 0, a.ny), f, g, step_seed, cd);
+        if (MODE == kSweepDiag) diag_row(acc, cd);
     }
     block_epilogue<real, PROB, MODE>(a, bx, band, gridDim.x, acc, sh);
 }
