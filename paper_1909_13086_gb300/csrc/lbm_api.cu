@@ -647,6 +647,11 @@ int lbm_diagnostics(lbm_handle h, lbm_diag *out) {
     DevRecord r;
     CUDA_TRY(h, cudaMemcpyAsync(&r, h->rec, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    // a timeout comes first: the sweep that ran out may not have reached the fold
+    if (r.timeout != 0.0)
+        return set_err(h, LBM_ERR_TIMEOUT,
+                       "a bounded device wait of the staged sweep ran out; the populations since are not "
+                       "valid (lbm_set_params or lbm_write_populations resets the state)");
     if (r.valid != 1.0 || (long long)r.step != h->step)
         return set_err(h, LBM_ERR_STATE, "no diagnostics for the current step");
     const double P = (double)h->nx * (double)h->ny;
@@ -659,10 +664,6 @@ int lbm_diagnostics(lbm_handle h, lbm_diag *out) {
     out->front_x = r.melt_sum / (double)h->ny;
     out->max_u = r.max_u;
     out->nan_flag = r.nan_flag != 0.0 ? 1 : 0;
-    if (r.timeout != 0.0)
-        return set_err(h, LBM_ERR_TIMEOUT,
-                       "a bounded device wait of the staged sweep ran out; the populations since are not "
-                       "valid (lbm_set_params or lbm_write_populations resets the state)");
     if (out->nan_flag) return set_err(h, LBM_ERR_DIVERGED, "non-finite H or rho at step %lld", h->step);
     return LBM_OK;
 }
@@ -721,6 +722,8 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
     h->step = step;
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
+    // both tickets back to zero (a sweep cut short by a timeout may leave one taken)
+    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned), h->stream));
     const unsigned long long counter = (unsigned long long)step;
     CUDA_TRY(h, cudaMemcpyAsync(&h->rec->counter, &counter, sizeof(counter), cudaMemcpyHostToDevice,
                                 h->stream));
