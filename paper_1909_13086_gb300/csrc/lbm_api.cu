@@ -35,10 +35,14 @@ void *g_alloc_ctx = nullptr;
 
 constexpr int kDefaultRows = 1;      // rows walked by each thread of a block (tuned on GB300)
 constexpr int kDefaultPrefetch = 4;  // L2 prefetch distance in rows (tuned on GB300)
-// 16-bit storage: a block's loads take as long as FP32's for half the bytes, so
-// the L2 prefetch pays further ahead (2048 x 1024 cavity on GB300: 8 rows
-// 38.6 us, 24 rows 38.3 us FP16-SR; 8 rows 35.1 us, 24 rows 33.6 us FP16).
-constexpr int kDefaultPrefetch16 = 24;
+// 16-bit storage is bound by instruction issue, and a thread's set-up (indices,
+// the rounding seed, the block's tail) costs ~115 instructions against ~316
+// per cell: 3 rows per thread spread it, with every row of a block prefetched
+// 8 rows ahead (2048 x 1024 BF16-SR cavity on GB300: 1 row 31.2 us, 2 rows
+// 28.6, 3 rows 27.9, 4 rows 29.9, 6 rows 30.0 us per step).  FP32 is memory
+// bound and fastest at 1 row (1 / 2 / 3 / 4 rows: 44.9 / 46.0 / 47.5 / 50.6 us).
+constexpr int kDefaultRows16 = 3;
+constexpr int kDefaultPrefetch16 = 8;
 constexpr int kDefaultGraphChunk = 128;  // longest graph-replayed piece (0 = direct launches)
 constexpr int kGraphCache = 16;          // cached piece graphs per handle
 
@@ -501,7 +505,10 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
     }
     h->esize = precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
     h->ntx = (nx + kTW - 1) / kTW;
-    if (h->esize == 2) h->prefetch = kDefaultPrefetch16;
+    if (h->esize == 2) {
+        h->rows = kDefaultRows16;
+        h->prefetch = kDefaultPrefetch16;
+    }
     set_grid(h);
     h->alloc = g_alloc;
     h->release = g_free;
@@ -867,8 +874,8 @@ extern "C" int lbm_autotune(lbm_handle h, int steps_per_trial, int *rows_out, in
         if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
             rc = set_err(h, LBM_ERR_CUDA, "lbm_autotune: cudaEventCreate failed");
         best.us_per_step = 1e30f;
-        const int rows_c[] = {1, 2, 4};
-        const int pf_c[] = {0, 2, 4, 8, 16, 32};
+        const int rows_c[] = {1, 2, 3, 4};
+        const int pf_c[] = {0, 2, 4, 8, 16, 24, 32};
         for (int rows : rows_c) {
             if (rc != LBM_OK || rows > h->ny) break;
             for (int pf : pf_c) {
@@ -975,12 +982,12 @@ template <typename real>
 size_t entry_bytes() { return sizeof(BatchEntry<real>); }
 
 // Default launch shape of a batch, whatever the members' own lbm_set_launch
-// settings: 1 row per block (4 with 16-bit storage), L2 prefetch 4 rows ahead
+// settings: 1 row per block (3 with 16-bit storage), L2 prefetch 4 rows ahead
 // (8), blocks of a one-size batch interleaved over the members -- what
 // lbm_batch_autotune picks for 64 cavities of 256 x 128 on GB300 (FP32 54.5 ->
-// 47.0 us per step against 2 rows member by member; BF16-SR 43.3 -> 39.5 us).
+// 47.0 us per step against 2 rows member by member; BF16-SR 43.3 -> 35.2 us).
 // Results do not depend on it.
-constexpr int kBatchRows32 = 1, kBatchRows16 = 4, kBatchPrefetch32 = 4, kBatchPrefetch16 = 8;
+constexpr int kBatchRows32 = 1, kBatchRows16 = 3, kBatchPrefetch32 = 4, kBatchPrefetch16 = 8;
 
 template <typename real>
 void batch_build(lbm_batch_s *b) {
@@ -1312,7 +1319,7 @@ extern "C" int lbm_batch_autotune(lbm_batch b, int steps_per_trial, int *rows_ou
         if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
             rc = LBM_ERR_CUDA;
         const bool sixteen = b->members[0]->esize == 2;
-        const int rows_c[] = {1, 2, 4};
+        const int rows_c[] = {1, 2, 3, 4};
         const int pf32[] = {0, 4, 16}, pf16[] = {0, 8, 24};
         const int *pf_c = sixteen ? pf16 : pf32;
         const int ninter = b->members.size() > 1 ? 2 : 1;  // interleaving needs several members

@@ -977,11 +977,12 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
     const int x = bx * kTW + lx;
     const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
-    // Blocks are scheduled roughly in row order, so the row `prefetch` rows
-    // ahead belongs to a block that starts a little later: fetching it into L2
-    // now shortens that block's load latency.
-    if (a.prefetch > 0 && threadIdx.x == 0 && y0 + a.prefetch < a.ny)
-        prefetch_tile_row_l2(src + cell_index<S>(bx * kTW, y0 + a.prefetch, 0, a.ny));
+    // Blocks are scheduled roughly in row order, so the rows `prefetch` rows
+    // ahead belong to a block that starts a little later: fetching them into
+    // L2 now shortens that block's load latency.  One bulk prefetch per row of
+    // the block, each from its own thread.
+    if (a.prefetch > 0 && (int)threadIdx.x < y1 - y0 && y0 + a.prefetch + (int)threadIdx.x < a.ny)
+        prefetch_tile_row_l2(src + cell_index<S>(bx * kTW, y0 + a.prefetch + (int)threadIdx.x, 0, a.ny));
     const uint32_t step_seed = step_prologue<real, S, MODE>(a, bx, by);
     const bool active = x < a.nx;
     // the warp's 32 columns are clear of both side walls (warp-uniform)
