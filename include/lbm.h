@@ -149,7 +149,7 @@ int lbm_set_diag_every(lbm_handle h, long long k);
 /* Launch shape of the sweep (the tuner's knobs): rows of the lattice walked by
  * each thread of a block (1 to 1024, default 1, or 3 with 16-bit storage);
  * the distance, in rows, at which each block asks L2 to prefetch a later
- * block's tile rows (0 = off, default 4, or 8 with 16-bit storage); and
+ * block's tile rows (0 = off, default 16, or 32 with 16-bit storage); and
  * graph_chunk, the longest piece
  * of sweeps lbm_step replays from a CUDA graph (0 = launch every sweep
  * directly; default 128).
@@ -210,7 +210,7 @@ typedef struct {
 int lbm_get_launch_stats(lbm_handle h, lbm_launch_stats *out);
 
 /* Autotuner: times every launch shape of a small candidate set (rows per block
- * 1, 2, 3, 4; prefetch distance 0, 2, 4, 8, 16, 24, 32 rows) for steps_per_trial
+ * 1, 2, 3, 4; prefetch distance 0, 2, 4, 8, 16, 24, 32, 48 rows) for steps_per_trial
  * steps each (best of two, after a warm-up) on a scratch lattice with the
  * handle's size, precision and parameters -- the handle's own state is not
  * touched, but the scratch lattice is allocated and freed -- and applies the
@@ -309,8 +309,8 @@ int lbm_batch_count(lbm_batch b, int *count);
 int lbm_batch_step(lbm_batch b, long long n);
 
 /* Launch shape of the batch's step kernel: rows of a member walked by each
- * block (0 = the default: 1, or 3 with 16-bit storage; up to 1024), the L2
- * prefetch distance in rows (-1 = the default: 4, or 8 with 16-bit storage),
+ * block (0 = the default: 2, or 4 with 16-bit storage; up to 1024), the L2
+ * prefetch distance in rows (-1 = the default: 4),
  * and interleave = 1 (the default) to number the blocks of a one-size batch
  * member after member (block b belongs to member b mod n) instead of member
  * by member (0; a batch whose members' block counts differ is always member
@@ -319,7 +319,7 @@ int lbm_batch_step(lbm_batch b, long long n);
 int lbm_batch_set_launch(lbm_batch b, int rows_per_block, int prefetch_rows, int interleave);
 
 /* Autotuner for a batch: times rows per block (1, 2, 3, 4) x prefetch distance
- * (0, 4, 16 rows; 0, 8, 24 with 16-bit storage) x block order (member by
+ * (0, 4, 8, 16 rows) x block order (member by
  * member, interleaved) for steps_per_trial steps each (best of three, after a
  * warm-up) on scratch lattices of the batch's composition -- the same sizes,
  * precision and parameters, allocated and freed here; the members' states are

@@ -33,16 +33,18 @@ lbm_alloc_fn g_alloc = nullptr;
 lbm_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
 
-constexpr int kDefaultRows = 1;      // rows walked by each thread of a block (tuned on GB300)
-constexpr int kDefaultPrefetch = 4;  // L2 prefetch distance in rows (tuned on GB300)
+constexpr int kDefaultRows = 1;       // rows walked by each thread of a block (tuned on GB300)
+constexpr int kDefaultPrefetch = 16;  // L2 prefetch distance in rows (tuned on GB300)
 // 16-bit storage is bound by instruction issue, and a thread's set-up (indices,
 // the rounding seed, the block's tail) costs ~115 instructions against ~316
 // per cell: 3 rows per thread spread it, with every row of a block prefetched
-// 8 rows ahead (2048 x 1024 BF16-SR cavity on GB300: 1 row 31.2 us, 2 rows
-// 28.6, 3 rows 27.9, 4 rows 29.9, 6 rows 30.0 us per step).  FP32 is memory
-// bound and fastest at 1 row (1 / 2 / 3 / 4 rows: 44.9 / 46.0 / 47.5 / 50.6 us).
+// (2048 x 1024 BF16-SR cavity on GB300, prefetch 8: 1 row 31.2 us, 2 rows
+// 28.6, 3 rows 27.9, 4 rows 29.9, 6 rows 30.0 us per step; with the
+// alternating sweep direction, 3 rows: prefetch 8 / 16 / 32 / 48 26.5 / 26.5 /
+// 26.3 / 26.2 us).  FP32 is memory bound and fastest at 1 row (2 rows: +0.6
+// us; prefetch 4 / 16 / 32: 41.8 / 41.5 / 41.4 us).
 constexpr int kDefaultRows16 = 3;
-constexpr int kDefaultPrefetch16 = 8;
+constexpr int kDefaultPrefetch16 = 32;
 constexpr int kDefaultGraphChunk = 128;  // longest graph-replayed piece (0 = direct launches)
 constexpr int kGraphCache = 16;          // cached piece graphs per handle
 
@@ -311,8 +313,6 @@ int launch_one(lbm_s *h, bool diag) {
     h->step = next;
     return LBM_OK;
 }
-
-bool diag_step(const lbm_s *h, long long step) { return h->diag_every > 0 && step % h->diag_every == 0; }
 
 void drop_graphs(lbm_s *h) {
     for (ChunkGraph &g : h->graphs) {
@@ -875,7 +875,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps_per_trial, int *rows_out, in
             rc = set_err(h, LBM_ERR_CUDA, "lbm_autotune: cudaEventCreate failed");
         best.us_per_step = 1e30f;
         const int rows_c[] = {1, 2, 3, 4};
-        const int pf_c[] = {0, 2, 4, 8, 16, 24, 32};
+        const int pf_c[] = {0, 2, 4, 8, 16, 24, 32, 48};
         for (int rows : rows_c) {
             if (rc != LBM_OK || rows > h->ny) break;
             for (int pf : pf_c) {
@@ -934,8 +934,8 @@ struct lbm_batch_s {
     std::vector<int> host_parity;
     int nblocks = 0;
     int uniform = 0;          // blocks per member when all members have the same count
-    int rows = 0;             // launch shape: rows per block (0: 1, or 4 with 16-bit storage),
-    int prefetch = -1;        // L2 prefetch distance (-1: 4 rows, 8 with 16-bit storage),
+    int rows = 0;             // launch shape: rows per block (0: 2, or 4 with 16-bit storage),
+    int prefetch = -1;        // L2 prefetch distance (-1: 4 rows),
     int interleave = 1;       // interleaved block order (uniform batches only; see batch_kernel)
     bool dirty = true;        // table must be rebuilt and uploaded
     int precision = -1, problem = -1, flow = -1;
@@ -982,12 +982,14 @@ template <typename real>
 size_t entry_bytes() { return sizeof(BatchEntry<real>); }
 
 // Default launch shape of a batch, whatever the members' own lbm_set_launch
-// settings: 1 row per block (3 with 16-bit storage), L2 prefetch 4 rows ahead
-// (8), blocks of a one-size batch interleaved over the members -- what
-// lbm_batch_autotune picks for 64 cavities of 256 x 128 on GB300 (FP32 54.5 ->
-// 47.0 us per step against 2 rows member by member; BF16-SR 43.3 -> 35.2 us).
-// Results do not depend on it.
-constexpr int kBatchRows32 = 1, kBatchRows16 = 3, kBatchPrefetch32 = 4, kBatchPrefetch16 = 8;
+// settings: 2 rows per block (4 with 16-bit storage), L2 prefetch 4 rows
+// ahead, blocks of a one-size batch interleaved over the members -- the
+// fastest shapes for 64 cavities of 256 x 128 on GB300 (FP32 46.1 us per
+// step, 55.9 with 2 rows member by member and no alternating direction;
+// BF16-SR 32.1 us, 43.3).  Longer prefetch distances run ahead of a small
+// member's sweep (FP32, 2 rows: prefetch 4 / 8 / 16 / 32 46.1 / 47.4 / 51.5 /
+// 57.5 us).  Results do not depend on it.
+constexpr int kBatchRows32 = 2, kBatchRows16 = 4, kBatchPrefetch32 = 4, kBatchPrefetch16 = 4;
 
 template <typename real>
 void batch_build(lbm_batch_s *b) {
@@ -1318,14 +1320,12 @@ extern "C" int lbm_batch_autotune(lbm_batch b, int steps_per_trial, int *rows_ou
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
             rc = LBM_ERR_CUDA;
-        const bool sixteen = b->members[0]->esize == 2;
         const int rows_c[] = {1, 2, 3, 4};
-        const int pf32[] = {0, 4, 16}, pf16[] = {0, 8, 24};
-        const int *pf_c = sixteen ? pf16 : pf32;
+        const int pf_c[] = {0, 4, 8, 16};
         const int ninter = b->members.size() > 1 ? 2 : 1;  // interleaving needs several members
         best.us_per_step = 1e30f;
         for (int rows : rows_c) {
-            for (int k = 0; k < 3 && rc == LBM_OK; ++k) {
+            for (int k = 0; k < 4 && rc == LBM_OK; ++k) {
                 for (int il = 0; il < ninter && rc == LBM_OK; ++il) {
                     rc = lbm_batch_set_launch(t, rows, pf_c[k], il);
                     if (rc == LBM_OK) rc = lbm_batch_step(t, 4);  // warm-up, table upload

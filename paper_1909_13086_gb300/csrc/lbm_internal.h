@@ -61,10 +61,12 @@ struct SweepArgs {
                            // set to w_i (they are never rewritten when flow is off)
     int nx, ny;            // lattice size
     int ntx;               // number of column tiles
-    int parity;            // index of the source buffer (selects the rounding seed word)
+    int parity;            // index of the source buffer (selects the rounding seed word
+                           // and the direction of the sweep over the row bands)
     int rows;              // rows per block (each thread walks them)
-    int prefetch;          // > 0: each block asks L2 for the tile row `prefetch`
-                           // rows below its own (one bulk prefetch per block)
+    int prefetch;          // > 0: each block asks L2 for the tile rows `prefetch`
+                           // rows ahead of its own in the sweep's direction
+                           // (one bulk prefetch per row)
     real k0, k1, k2;       // g rates (Eq. 2)
     real k0f, k1f, k2f;    // f rates
     real Lh, gbeta;        // latent heat, g*beta

@@ -964,6 +964,21 @@ __device__ __forceinline__ void block_epilogue(const SweepArgs<real> &a, int bx,
     if (MODE == kSweepDiag) diag_partial_rows(acc, a.dpart, (size_t)bx + (size_t)by * gx, sh);
 }
 
+// Row-block order of a sweep: the row band a block of launch position k (of
+// gy bands) works on.  Successive steps visit the interior bands in opposite
+// directions (rev = 1: descending; the source buffer's parity alternates with
+// the step), so that a step starts on the rows the previous step wrote last,
+// which are still in L2: the two population buffers of a large lattice exceed
+// L2, and a sweep in a fixed direction would start on rows long evicted.  The
+// two wall bands (boundary pulls; the bottom one also folds the heated-wall
+// inflow in the cavity) go first in both directions, so that they do not form
+// the launch's tail.  A permutation of 0 .. gy - 1 for either direction.
+__device__ __forceinline__ int row_band(const int k, const int gy, const int rev) {
+    if (k == 0 || gy < 3) return k;
+    if (k == 1) return gy - 1;
+    return rev ? gy - k : k - 1;
+}
+
 // One block's work: the tile column bx (kTW cells) and the row band by
 // (a.rows rows) of the lattice described by a; gx is the number of tile
 // columns (for the block's partial-sum slot).  Called by lattice_kernel (one
@@ -977,12 +992,15 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
     const int x = bx * kTW + lx;
     const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
-    // Blocks are scheduled roughly in row order, so the rows `prefetch` rows
-    // ahead belong to a block that starts a little later: fetching them into
-    // L2 now shortens that block's load latency.  One bulk prefetch per row of
-    // the block, each from its own thread.
-    if (a.prefetch > 0 && (int)threadIdx.x < y1 - y0 && y0 + a.prefetch + (int)threadIdx.x < a.ny)
-        prefetch_tile_row_l2(src + cell_index<S>(bx * kTW, y0 + a.prefetch + (int)threadIdx.x, 0, a.ny));
+    // Blocks are scheduled roughly in launch order, so the rows `prefetch`
+    // rows ahead in the sweep's direction (row_band) belong to a block that
+    // starts a little later: fetching them into L2 now shortens that block's
+    // load latency.  One bulk prefetch per row of the block, each from its own
+    // thread.
+    if (a.prefetch > 0 && (int)threadIdx.x < y1 - y0) {
+        const int yp = (a.parity ? y0 - a.prefetch : y0 + a.prefetch) + (int)threadIdx.x;
+        if (yp >= 0 && yp < a.ny) prefetch_tile_row_l2(src + cell_index<S>(bx * kTW, yp, 0, a.ny));
+    }
     const uint32_t step_seed = step_prologue<real, S, MODE>(a, bx, by);
     const bool active = x < a.nx;
     // the warp's 32 columns are clear of both side walls (warp-uniform)
@@ -1028,7 +1046,8 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     __shared__ double sh[32 * 4];
     pdl_launch_dependents();
     pdl_wait();  // the previous sweep's populations, tickets and record
-    sweep_block<real, S, PROB, FLOW, MODE>(a, blockIdx.x, blockIdx.y, gridDim.x, sh);
+    sweep_block<real, S, PROB, FLOW, MODE>(a, blockIdx.x, row_band((int)blockIdx.y, (int)gridDim.y, a.parity),
+                                           gridDim.x, sh);
 }
 
 // ---- the staged sweep (16-bit storage) ----
@@ -1336,7 +1355,7 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     pdl_wait();
     const BatchEntry<real> &e = *reinterpret_cast<const BatchEntry<real> *>(entry_sh);
     const int l = (uniform > 0 && interleave) ? (int)(blockIdx.x / (unsigned)n) : (int)blockIdx.x - e.start;
-    sweep_block<real, S, PROB, FLOW, MODE>(e.a[meta[1]], l % e.gx, l / e.gx, e.gx, sh);
+    sweep_block<real, S, PROB, FLOW, MODE>(e.a[meta[1]], l % e.gx, row_band(l / e.gx, e.gy, meta[1]), e.gx, sh);
 }
 
 // Per-entry diagnostics fold after a diagnostic batch step: block r folds the

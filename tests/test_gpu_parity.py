@@ -463,11 +463,35 @@ def test_graph_replay_matches_direct_launches(stream, prec):
         assert d == d0
 
 
-def test_launch_shape_does_not_change_populations(stream):
+@pytest.mark.parametrize("problem", ["cavity", "stefan"])
+@pytest.mark.parametrize("ny", [3, 4, 5, 7, 10])
+def test_row_band_order_both_directions(orc, stream, problem, ny):
+    """Successive sweeps visit the row bands in opposite directions, the two
+    wall bands first; every band count (1 to 10 bands, a ragged last band)
+    and both directions (odd and even steps) match the oracle."""
+    nx = 130
+    if problem == "cavity":
+        p = workloads.params(Ra=1e5, strip_center=0.45, strip_width=0.3)
+    else:
+        p = workloads.stefan_1024x4(Ste=1.0, nx=nx)[2]
+    ref = orc.Oracle(nx, ny, **p)
+    ref.step(9)
+    want = ref.fields()
+    for rows in (1, 2, 3, 4):
+        lat = lbm.Lattice(nx, ny, p, precision="fp64", stream=stream)
+        lbm.lbm_set_launch(lat.h, rows, 2, 0)
+        lat.step(9)
+        assert_fields_fp64(lat.fields(), want)
+        assert lat.diagnostics()["Q_cum"] == pytest.approx(ref.diagnostics()["Q_cum"], rel=1e-12, abs=1e-15)
+        lat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16sr"])
+def test_launch_shape_does_not_change_populations(stream, prec):
     nx, ny, p = 260, 45, workloads.params(Ra=1e5)
     ref = None
     for rows, pf in ((1, 0), (1, 4), (3, 2), (8, 64)):
-        lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+        lat = lbm.Lattice(nx, ny, p, precision=prec, stream=stream)
         lbm.lbm_set_launch(lat.h, rows, pf, 16)
         lat.step(120)
         f, g, _ = lat.populations()
