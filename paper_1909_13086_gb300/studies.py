@@ -18,6 +18,10 @@
   0.5, 0.9, 0.95 and 0.99: the ordering the paper reports (Sec. 3.2, Sec. 4)
   is that the centred strip melts the cavity first.  Long runs resume from a
   checkpoint of the FP32 (or FP64) populations.
+* ``precision_study`` -- the storage precisions against the FP64 path on the
+  2048 x 1024 cavity heated from below (Ra 1e8, Pr 1, Ste 1, strip a quarter
+  of the width) at several strip centres: the largest melt-fraction difference
+  over the run and the relative difference of the time-mean Nusselt number.
 
 Lattice units (reading of Sec. 3.1's mixed units): dt follows from k1 through
 Eq. 5, dt = dx^2 (1/k1 - 1/2) / (3 alpha), so t = 25 is 25 / dt steps and the
@@ -109,6 +113,63 @@ def cavity_location_sweep(fo_end: float = 0.01, n: int = 512, centers=(0.25, 0.3
         out[C] = hist
         lat.close()
     return out
+
+
+# The storage study: 2e5 steps of the 2048 x 1024 cavity, sampled every 1000.
+PRECISION_STUDY = dict(nx=2048, ny=1024, steps=200_000, every=1000, centers=(0.25, 0.5, 0.75),
+                       precisions=("fp32", "fp16", "bf16", "fp16sr", "bf16sr"))
+
+
+def run_history(lat, steps: int, every: int) -> dict:
+    """Advance `lat` by `steps` in pieces of at most `every`, sampling the melt
+    fraction after each piece; also the final cumulative heated-wall inflow."""
+    melt, done = [], 0
+    while done < steps:
+        k = min(every, steps - done)
+        lat.step(k)
+        done += k
+        melt.append(lat.diagnostics(raise_on_diverged=False)["melt_fraction"])
+    d = lat.diagnostics(raise_on_diverged=False)
+    return {"melt": melt, "Q_cum": d["Q_cum"], "final_melt": d["melt_fraction"],
+            "nan_flag": d["nan_flag"]}
+
+
+def compare_to_fp64(ref: dict, run: dict) -> dict:
+    """The largest melt-fraction difference over the samples, and the relative
+    difference of the time-mean Nusselt number: Nu is the inflow times the same
+    constant for both runs, so the mean of Nu over the run compares as the
+    cumulative inflow Q_cum does."""
+    m64, m = np.asarray(ref["melt"], np.float64), np.asarray(run["melt"], np.float64)
+    if m64.shape != m.shape:
+        raise ValueError("the two runs were sampled differently")
+    return {"melt_err_max": float(np.abs(m - m64).max()) if m.size else 0.0,
+            "mean_nu_rel_err": (run["Q_cum"] / ref["Q_cum"] - 1.0) if ref["Q_cum"] != 0.0 else math.nan,
+            "final_melt": run["final_melt"], "final_melt_fp64": ref["final_melt"],
+            "nan_flag": run["nan_flag"]}
+
+
+def precision_study(nx: int = 2048, ny: int = 1024, steps: int = 200_000, every: int = 1000,
+                    centers=(0.25, 0.5, 0.75), precisions=PRECISION_STUDY["precisions"],
+                    stream=None, make_lattice=None) -> list[dict]:
+    """Each storage precision against the FP64 path, strip centre by strip
+    centre (one row per centre and precision).  make_lattice(C, precision)
+    replaces the GPU lattice (host tests)."""
+    if make_lattice is None:
+        def make_lattice(C, precision):
+            p = workloads.params(Ra=1e8, strip_center=C)
+            return lbm.Lattice(nx, ny, p, precision=precision, stream=stream)
+    rows = []
+    for C in centers:
+        lat = make_lattice(C, "fp64")
+        ref = run_history(lat, steps, every)
+        lat.close()
+        for prec in precisions:
+            lat = make_lattice(C, prec)
+            res = run_history(lat, steps, every)
+            lat.close()
+            rows.append({"C": C, "precision": prec, "steps": steps, "every": every,
+                         **compare_to_fp64(ref, res)})
+    return rows
 
 
 FULL_MELT_LEVELS = (0.5, 0.9, 0.95, 0.99)
@@ -223,10 +284,13 @@ def cavity_full_melt(n: int = 512, centers=(0.25, 0.375, 0.5), levels=FULL_MELT_
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description="the paper's Stefan and cavity-location studies")
-    ap.add_argument("--study", choices=("stefan", "cavity", "cavity-full"), default="stefan")
+    ap.add_argument("--study", choices=("stefan", "cavity", "cavity-full", "precision"), default="stefan")
     ap.add_argument("--fo", type=float, default=0.01)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--n", type=int, default=512, help="cavity-full: lattice size")
+    ap.add_argument("--steps", type=int, default=PRECISION_STUDY["steps"], help="precision: steps per run")
+    ap.add_argument("--every", type=int, default=PRECISION_STUDY["every"], help="precision: sample interval")
+    ap.add_argument("--size", default="2048x1024", help="precision: lattice size NXxNY")
     ap.add_argument("--fo-max", type=float, default=1.0, help="cavity-full: stop at this Fo")
     ap.add_argument("--checkpoint", default=None, help="cavity-full: resume from / save to")
     ap.add_argument("--max-seconds", type=float, default=None, help="cavity-full: wall budget")
@@ -238,6 +302,11 @@ def main(argv=None):
     s = torch.cuda.Stream()
     if args.study == "stefan":
         for row in stefan_k1_sweep(args.precision or "fp64", s.cuda_stream):
+            print(json.dumps(row), flush=True)
+    elif args.study == "precision":
+        nx, ny = (int(v) for v in args.size.split("x"))
+        precs = tuple(args.precision.split(",")) if args.precision else PRECISION_STUDY["precisions"]
+        for row in precision_study(nx, ny, args.steps, args.every, precisions=precs, stream=s.cuda_stream):
             print(json.dumps(row), flush=True)
     elif args.study == "cavity":
         res = cavity_location_sweep(args.fo, precision=args.precision or "fp32", stream=s.cuda_stream)

@@ -120,3 +120,41 @@ def test_checkpoint_of_another_run_and_16_bit_are_rejected(tmp_path):
             make_lattice=lambda C: FakeLattice(RATES[C]), make_batch=lambda k: FakeBatch(k, []))
     with pytest.raises(ValueError):
         studies.cavity_full_melt(n=8, precision="bf16sr", checkpoint=str(tmp_path / "x.npz"))
+
+
+class FakeRun:
+    """Melt fraction and inflow growing at fixed rates; `bias` stands in for a
+    storage precision's departure from the FP64 run."""
+    def __init__(self, bias):
+        self.bias, self.n = bias, 0
+
+    def step(self, k):
+        self.n += k
+
+    def diagnostics(self, raise_on_diverged=True):
+        return {"melt_fraction": 1e-5 * self.n * (1.0 + self.bias), "Q_cum": 2.0 * self.n * (1.0 + self.bias),
+                "nan_flag": 0}
+
+    def close(self):
+        pass
+
+
+def test_precision_study_compares_each_precision_with_fp64():
+    bias = {"fp64": 0.0, "fp32": 1e-3, "bf16sr": -0.02}
+    rows = studies.precision_study(steps=2500, every=1000, centers=(0.25, 0.5),
+                                   precisions=("fp32", "bf16sr"),
+                                   make_lattice=lambda C, prec: FakeRun(bias[prec]))
+    assert [(r["C"], r["precision"]) for r in rows] == [(0.25, "fp32"), (0.25, "bf16sr"),
+                                                         (0.5, "fp32"), (0.5, "bf16sr")]
+    for r in rows:
+        b = bias[r["precision"]]
+        # samples after 1000, 2000 and the last 500 steps: the largest gap is at the end
+        assert r["melt_err_max"] == pytest.approx(abs(b) * 1e-5 * 2500)
+        assert r["mean_nu_rel_err"] == pytest.approx(b)
+        assert r["final_melt_fp64"] == pytest.approx(1e-5 * 2500)
+
+
+def test_compare_to_fp64_rejects_different_sampling():
+    with pytest.raises(ValueError):
+        studies.compare_to_fp64({"melt": [0.1, 0.2], "Q_cum": 1.0, "final_melt": 0.2, "nan_flag": 0},
+                                {"melt": [0.1], "Q_cum": 1.0, "final_melt": 0.1, "nan_flag": 0})
