@@ -184,7 +184,9 @@ def lbm_set_diag_every(h, k: int) -> None:
     _check(lib().lbm_set_diag_every(h, int(k)), h)
 
 
-def lbm_set_launch(h, rows: int = 1, prefetch: int = 4, graph_chunk: int = 128) -> None:
+def lbm_set_launch(h, rows: int = 1, prefetch: int = 16, graph_chunk: int = 128) -> None:
+    """Launch shape (the defaults are the library's FP32 ones; with 16-bit
+    storage the library starts from 3 rows and prefetch 32)."""
     _check(lib().lbm_set_launch(h, int(rows), int(prefetch), int(graph_chunk)), h)
 
 
