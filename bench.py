@@ -400,10 +400,18 @@ def run_ours(args) -> None:
     kernel_s = elapsed / args.steps
     alg_bytes = BYTES_PER_LUP[prec] * cells
     achieved = alg_bytes / kernel_s / 1e9
+    traffic = profiled_traffic(prec)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(prec),
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} HBM copy bandwidth",
                 "algorithmic_bytes_per_launch": alg_bytes}
+    if traffic:
+        # The DRAM side: the profiled bytes per launch (warm L2, as in this
+        # loop) over the measured time.  A step that starts on rows the
+        # previous one left in L2 moves fewer bytes than it reads and writes,
+        # so `frac` (algorithmic bytes) can exceed 1 while this stays below.
+        roofline["dram_achieved"] = round(traffic / kernel_s / 1e9, 1)
+        roofline["dram_frac"] = round(traffic / kernel_s / 1e9 / peak, 4)
     if prec == "fp64":
         # the FP64 sweep is bound by GB300's FP64 pipe, not by HBM
         flops = FP64_FLOPS_PER_LUP * cells
