@@ -194,10 +194,31 @@ def _paper_cavity(n, C, precision, stream):
     return lbm.Lattice(n, n, p, precision=precision, stream=stream)
 
 
+class SoloSteps:
+    """The batch interface over lattices stepped one by one (the single-lattice
+    sweep, for a study of one large cavity)."""
+
+    def __init__(self, k=None):
+        self.members = []
+
+    def add(self, lat):
+        self.members.append(lat)
+
+    def remove(self, lat):
+        self.members.remove(lat)
+
+    def step(self, k):
+        for lat in self.members:
+            lat.step(k)
+
+    def close(self):
+        self.members = []
+
+
 def cavity_full_melt(n: int = 512, centers=(0.25, 0.375, 0.5), levels=FULL_MELT_LEVELS,
                      fo_max: float = 1.0, sample_fo: float = 0.002, precision: str = "fp32",
                      stream=None, checkpoint: str | None = None, max_seconds: float | None = None,
-                     make_lattice=None, make_batch=None) -> dict:
+                     make_lattice=None, make_batch=None, href: int | None = None) -> dict:
     """Run the paper's cavities (Sec. 3.2) to full melting, all in one batch.
 
     Every `sample_fo` of Fourier number each running cavity's diagnostics are
@@ -207,7 +228,8 @@ def cavity_full_melt(n: int = 512, centers=(0.25, 0.375, 0.5), levels=FULL_MELT_
     writes `checkpoint` (populations, step and history of each cavity) and
     returns with complete = False; a later call with the same checkpoint path
     resumes where it stopped and, for FP32 and FP64, ends bitwise where an
-    uninterrupted run ends."""
+    uninterrupted run ends.  The Fourier number is alpha t / href^2 with href
+    the cavity height (n for the paper's square cavities)."""
     import os
     import time
 
@@ -217,7 +239,8 @@ def cavity_full_melt(n: int = 512, centers=(0.25, 0.375, 0.5), levels=FULL_MELT_
     make_batch = make_batch or (lambda k: lbm.Batch(k, stream))
     lats = [make_lattice(C) for C in centers]
     alpha = lats[0].derived()["alpha"]
-    chunk = max(1, int(round(sample_fo * n * n / alpha)))
+    L2 = float(href or n) ** 2
+    chunk = max(1, int(round(sample_fo * L2 / alpha)))
     target = max(levels)
     hist = [[] for _ in centers]
     state = ["running"] * len(centers)
@@ -232,7 +255,7 @@ def cavity_full_melt(n: int = 512, centers=(0.25, 0.375, 0.5), levels=FULL_MELT_
     else:  # the initial state is the first sample
         for i, lat in enumerate(lats):
             d = lat.diagnostics(raise_on_diverged=False)
-            hist[i].append((d["step"] * alpha / (n * n), d["melt_fraction"], d["Nu"],
+            hist[i].append((d["step"] * alpha / L2, d["melt_fraction"], d["Nu"],
                             float(d["nan_flag"])))
     batch = make_batch(len(centers))
     for i, lat in enumerate(lats):
@@ -246,7 +269,7 @@ def cavity_full_melt(n: int = 512, centers=(0.25, 0.375, 0.5), levels=FULL_MELT_
             if state[i] != "running":
                 continue
             d = lat.diagnostics(raise_on_diverged=False)
-            fo = d["step"] * alpha / (n * n)
+            fo = d["step"] * alpha / L2
             hist[i].append((fo, d["melt_fraction"], d["Nu"], float(d["nan_flag"])))
             if d["nan_flag"]:
                 state[i] = "diverged"
@@ -282,9 +305,34 @@ def cavity_full_melt(n: int = 512, centers=(0.25, 0.375, 0.5), levels=FULL_MELT_
                      for i, C in enumerate(centers)}}
 
 
+def production_full_melt(center: float = 0.5, sample_fo: float = 0.002, fo_max: float = 1.0,
+                          max_seconds: float | None = None, stream=None, make_lattice=None) -> dict:
+    """The 2048 x 1024 production cavity (Ra 1e8, Pr 1, Ste 1, Ma 0.1, FP32
+    populations and arithmetic, heated strip a quarter of the width) run to
+    full melting on the single-lattice sweep: the melt-fraction and Nusselt
+    history against Fo = alpha t / H^2 (H = 1024, the height), and the run's
+    throughput over its wall time (sampling included)."""
+    import time
+
+    nx, ny, _ = workloads.cavity_2048x1024(center)
+    make_lattice = make_lattice or (lambda C: lbm.Lattice(nx, ny, workloads.cavity_2048x1024(C)[2],
+                                                          precision="fp32", stream=stream))
+    t0 = time.monotonic()
+    res = cavity_full_melt(n=nx, centers=(center,), fo_max=fo_max, sample_fo=sample_fo,
+                           precision="fp32", stream=stream, max_seconds=max_seconds,
+                           make_lattice=make_lattice, make_batch=SoloSteps, href=ny)
+    wall = time.monotonic() - t0
+    run = res["runs"][str(center)]
+    steps = int(round(run["final"][0] * ny * ny / res["alpha"])) if run["final"] else 0
+    res.update({"nx": nx, "ny": ny, "steps": steps, "wall_s": wall,
+                "mlups_wall": steps * nx * ny / wall / 1e6 if wall > 0 else 0.0})
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="the paper's Stefan and cavity-location studies")
-    ap.add_argument("--study", choices=("stefan", "cavity", "cavity-full", "precision"), default="stefan")
+    ap.add_argument("--study", choices=("stefan", "cavity", "cavity-full", "precision", "production-full"),
+                    default="stefan")
     ap.add_argument("--fo", type=float, default=0.01)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--n", type=int, default=512, help="cavity-full: lattice size")
@@ -303,6 +351,14 @@ def main(argv=None):
     if args.study == "stefan":
         for row in stefan_k1_sweep(args.precision or "fp64", s.cuda_stream):
             print(json.dumps(row), flush=True)
+    elif args.study == "production-full":
+        res = production_full_melt(fo_max=args.fo_max, max_seconds=args.max_seconds, stream=s.cuda_stream)
+        if args.out:
+            with open(args.out, "w") as fh:
+                json.dump(res, fh)
+        run = res["runs"]["0.5"]
+        print(json.dumps({k: v for k, v in res.items() if k != "runs"} |
+                         {"state": run["state"], "fo_at": run["fo_at"], "final": run["final"]}), flush=True)
     elif args.study == "precision":
         nx, ny = (int(v) for v in args.size.split("x"))
         precs = tuple(args.precision.split(",")) if args.precision else PRECISION_STUDY["precisions"]

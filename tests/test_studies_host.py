@@ -158,3 +158,24 @@ def test_compare_to_fp64_rejects_different_sampling():
     with pytest.raises(ValueError):
         studies.compare_to_fp64({"melt": [0.1, 0.2], "Q_cum": 1.0, "final_melt": 0.2, "nan_flag": 0},
                                 {"melt": [0.1], "Q_cum": 1.0, "final_melt": 0.1, "nan_flag": 0})
+
+
+class FakeSoloLattice(FakeLattice):
+    """A lattice stepped on its own (the single-lattice path)."""
+    def step(self, k):
+        self.advance(k)
+
+
+def test_production_full_melt_uses_the_cavity_height_for_fo():
+    """Fo = alpha t / H^2 with H = 1024 (not the width), one sample every
+    0.002 of Fo, the run ends at melt fraction 0.99 and reports its steps."""
+    rate = 1.0 / 2e7   # melt fraction per step: 0.99 after 1.98e7 steps
+    res = studies.production_full_melt(sample_fo=0.002, make_lattice=lambda C: FakeSoloLattice(rate))
+    H2, alpha = 1024.0 ** 2, 0.01
+    assert res["steps_per_sample"] == round(0.002 * H2 / alpha)
+    run = res["runs"]["0.5"]
+    assert run["state"] == "melted" and res["complete"]
+    # the crossing of 0.5, interpolated between samples, sits at 1e7 steps
+    assert run["fo_at"]["0.5"] == pytest.approx(1e7 * alpha / H2, rel=1e-9)
+    assert res["steps"] == round(run["final"][0] * H2 / alpha)
+    assert res["nx"] == 2048 and res["ny"] == 1024 and res["mlups_wall"] > 0
