@@ -152,7 +152,10 @@ int lbm_set_diag_every(lbm_handle h, long long k);
  * block's tile rows (0 = off, default 16, or 32 with 16-bit storage); and
  * graph_chunk, the longest piece
  * of sweeps lbm_step replays from a CUDA graph (0 = launch every sweep
- * directly; default 128).
+ * directly; default 128).  Successive sweeps visit the lattice's row bands in
+ * opposite directions (the two wall bands first), each starting on the rows
+ * the previous one wrote last, which are still in L2; the prefetch distance
+ * counts along the sweep's direction.
  *
  * How lbm_step enqueues its n sweeps: it cuts them into pieces that end at
  * the diagnostic sweeps (every diag_every-th step and the call's last one)
