@@ -73,11 +73,17 @@ def sweep_launches(warmup: int, steps: int) -> int:
 
 
 def workload_config(precision: str) -> dict:
+    one = precision == "fp32"   # the library's default streaming for FP32 (lbm_set_streaming)
+    mb = BYTES_PER_LUP[precision] * NX * NY / 2 / 1e6      # one buffer of populations
     return {"workload": f"cavity {NX}x{NY}, Ra 1e8, Pr 1, Ste 1, Ma 0.1, strip W/4 centred, "
                         f"{precision.upper()} populations",
             "nx": NX, "ny": NY, "precision": precision,
             "diagnostics": f"fused every {DIAG_EVERY} steps; heated-wall flux every step",
-            "l2": "inputs larger than L2 (2 x 151 MB populations), no flush"}
+            "streaming": ("one buffer (push / local sweeps), the call's last 1-2 sweeps over two buffers"
+                          if one else "two buffers"),
+            "l2": (f"inputs larger than L2 ({mb:.0f} MB of populations in the buffer a step reads and "
+                   "writes), no flush" if one else
+                   f"inputs larger than L2 (2 x {mb:.0f} MB populations), no flush")}
 
 
 # ------------------------------------------------------------ distributed

@@ -176,6 +176,31 @@ int lbm_set_diag_every(lbm_handle h, long long k);
  * follow the grouping of cells, to within FP64 rounding.  Errors: LBM_ERR_ARG. */
 int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int graph_chunk);
 
+/* How lbm_step moves the populations from one step to the next.
+ * LBM_STREAM_TWO_BUFFERS (the default): every sweep pulls from one buffer into
+ * the other.  LBM_STREAM_ONE_BUFFER: all but the last one or two sweeps of a
+ * call work in place in one buffer, alternating two sweeps (the AA pattern of
+ * Bailey et al., "Accelerating lattice Boltzmann fluid flow simulations using
+ * graphics processors", 2009): a push sweep that pulls as usual and puts
+ * each post-collision population f*_i(x) into slot opp(i) of cell x + c_i
+ * (its own slot i where x + c_i lies beyond a wall), then a local sweep that
+ * takes a cell's populations from its own slots (wall rules on the edge) and
+ * writes them back to their own slots, which leaves the usual layout.  Each
+ * cell reads and writes the same locations in either sweep.  The closing
+ * sweeps of a call run over the two buffers, so between calls the handle's
+ * state is exactly that of two-buffer streaming: results, fields, populations
+ * and checkpoints do not depend on the mode, bit for bit.  One buffer halves
+ * the working set of a step, so that more of what the previous step wrote is
+ * still in L2 when the next one reads it.  Both buffers stay allocated.  The
+ * staged 16-bit sweep, batches and lbm_step_static always use two buffers.
+ * Default (set by lbm_create): one buffer for LBM_FP32, whose sweep is bound
+ * by memory (2048 x 1024 cavity on GB300: 41.4 -> 37.0 us per step); two
+ * buffers for the 16-bit types, whose sweeps are bound by instruction issue
+ * and slow down with the push sweep's addressing, and for LBM_FP64, bound by
+ * its arithmetic.  Takes effect at the next lbm_step.  Errors: LBM_ERR_ARG. */
+enum { LBM_STREAM_TWO_BUFFERS = 0, LBM_STREAM_ONE_BUFFER = 1 };
+int lbm_set_streaming(lbm_handle h, int mode);
+
 /* Sweep kernel for 16-bit storage.  The staged sweep (an option for LBM_FP16,
  * LBM_BF16, LBM_FP16_SR and LBM_BF16_SR; off by default) gives each block a band of
  * consecutive rows of one 128-cell tile column and streams the tile rows it

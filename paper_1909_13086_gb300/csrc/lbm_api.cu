@@ -58,6 +58,8 @@ struct ChunkGraph {
     int parity = 0;
     int len = 0;
     bool diag = false;
+    bool one_buffer = false;  // sweeps of one-buffer streaming, from phase `phase`
+    int phase = 0;
     cudaGraphExec_t exec = nullptr;
     unsigned long long stamp = 0;
 };
@@ -79,6 +81,11 @@ struct lbm_s {
     void *buf[2] = {nullptr, nullptr};  // 18 planes each
     int cur = 0;                // buffer holding the current post-collision populations
     bool has_prev = false;      // buf[cur ^ 1] holds the previous step's populations
+    // lbm_set_streaming: 1 = one-buffer streaming for all but the last one or
+    // two sweeps of an lbm_step call; phase: 0 while buf[cur] holds the pull
+    // layout (always between calls), 1 after a push sweep
+    int streaming = LBM_STREAM_TWO_BUFFERS;  // set per precision by lbm_create
+    int phase = 0;
     long long step = 0;
     long long diag_every = 0;
     bool params_set = false;
@@ -314,6 +321,25 @@ int launch_one(lbm_s *h, bool diag) {
     return LBM_OK;
 }
 
+// One sweep of one-buffer streaming (Streaming in lbm_internal.h) in
+// buf[cur]: the push sweep at phase 0, the local sweep at phase 1.  The parity
+// word (rounding seed, sweep direction) alternates as it does over two
+// buffers, so the populations are bitwise those of the pull sweeps.
+template <typename real, typename S>
+int launch_one_aa(lbm_s *h, bool diag) {
+    const long long next = h->step + 1;
+    SweepArgs<real> a = make_args<real>(h, h->buf[h->cur], h->buf[h->cur]);
+    a.parity = h->cur ^ h->phase;
+    a.step = next;
+    cudaError_t e = launch_lattice<real, S>(a, h->p.problem, h->p.flow_on != 0, diag ? kSweepDiag : kSweep,
+                                         h->grid, h->block, h->stream, true, h->phase ? kAALocal : kAAPush);
+    if (e != cudaSuccess) return set_err(h, LBM_ERR_CUDA, "sweep launch failed: %s", cudaGetErrorString(e));
+    h->phase ^= 1;
+    h->has_prev = false;  // buf[cur ^ 1] is stale until the call's closing two-buffer sweeps
+    h->step = next;
+    return LBM_OK;
+}
+
 void drop_graphs(lbm_s *h) {
     for (ChunkGraph &g : h->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -327,7 +353,8 @@ void drop_graphs(lbm_s *h) {
 // counter, heated-wall sums, tickets, rounding seeds) lives in device memory,
 // so a captured piece replays correctly at any later step.
 template <typename real, typename S>
-int run_piece(lbm_s *h, long long len, bool diag) {
+int run_piece(lbm_s *h, long long len, bool diag, bool one_buffer = false) {
+    auto launch = [&](bool d) { return one_buffer ? launch_one_aa<real, S>(h, d) : launch_one<real, S>(h, d); };
     bool graphs = h->graph_chunk >= 2 && len >= 2 && len <= h->graph_chunk;
     if (graphs) {
         cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -336,7 +363,9 @@ int run_piece(lbm_s *h, long long len, bool diag) {
     ChunkGraph *slot = nullptr;
     if (graphs) {
         for (ChunkGraph &g : h->graphs)
-            if (g.used && g.parity == h->cur && g.len == len && g.diag == diag) slot = &g;
+            if (g.used && g.parity == h->cur && g.len == len && g.diag == diag && g.one_buffer == one_buffer &&
+                g.phase == h->phase)
+                slot = &g;
         if (!slot) {  // first sighting: remember it, launch directly
             ChunkGraph *victim = &h->graphs[0];
             for (ChunkGraph &g : h->graphs) {
@@ -349,18 +378,21 @@ int run_piece(lbm_s *h, long long len, bool diag) {
             victim->parity = h->cur;
             victim->len = (int)len;
             victim->diag = diag;
+            victim->one_buffer = one_buffer;
+            victim->phase = h->phase;
             victim->stamp = ++h->graph_clock;
             graphs = false;
         } else if (!slot->exec) {  // second sighting: capture it
-            const int cur0 = h->cur;
+            const int cur0 = h->cur, phase0 = h->phase;
             const long long step0 = h->step;
             const bool prev0 = h->has_prev;
             CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
             int rc = LBM_OK;
-            for (long long j = 0; j < len && rc == LBM_OK; ++j) rc = launch_one<real, S>(h, diag && j == len - 1);
+            for (long long j = 0; j < len && rc == LBM_OK; ++j) rc = launch(diag && j == len - 1);
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
             h->cur = cur0;
+            h->phase = phase0;
             h->step = step0;
             h->has_prev = prev0;
             if (rc != LBM_OK) {
@@ -381,14 +413,19 @@ int run_piece(lbm_s *h, long long len, bool diag) {
     if (graphs) {
         slot->stamp = ++h->graph_clock;
         CUDA_TRY(h, cudaGraphLaunch(slot->exec, h->stream));
-        h->cur ^= (int)(len & 1);
-        h->has_prev = true;
+        if (one_buffer) {
+            h->phase ^= (int)(len & 1);
+            h->has_prev = false;
+        } else {
+            h->cur ^= (int)(len & 1);
+            h->has_prev = true;
+        }
         h->step += len;
         h->stats.sweeps_replayed += len;
         return LBM_OK;
     }
     for (long long j = 0; j < len; ++j) {
-        const int rc = launch_one<real, S>(h, diag && j == len - 1);
+        const int rc = launch(diag && j == len - 1);
         if (rc != LBM_OK) return rc;
     }
     h->stats.sweeps_direct += len;
@@ -398,8 +435,35 @@ int run_piece(lbm_s *h, long long len, bool diag) {
 // n sweeps, cut into pieces that end at the diagnostic sweeps (every
 // diag_every-th step and the call's last one) and are at most graph_chunk
 // long: with diag_every = 100 every full piece is the same 100-sweep graph.
+//
+// With one-buffer streaming all but the last one or two sweeps of the call run
+// in buf[cur] (an even number, so that the buffer holds the pull layout again),
+// in pieces that end at the diagnostic steps; the closing sweeps run over the
+// two buffers, so that between calls buf[cur ^ 1] holds the previous step's
+// populations (the fields are recomputed from them) as with two buffers.
 template <typename real, typename S>
 int enqueue_steps(lbm_s *h, long long n) {
+    long long aa = 0;
+    if (h->streaming == LBM_STREAM_ONE_BUFFER && !use_staged(h) && n >= 3) aa = (n & 1) ? n - 1 : n - 2;
+    for (long long done = 0; done < aa;) {
+        long long len = aa - done;
+        bool diag = false;
+        if (h->diag_every > 0) {
+            const long long k = h->diag_every - h->step % h->diag_every;
+            if (k <= len) {
+                len = k;
+                diag = true;
+            }
+        }
+        if (h->graph_chunk >= 2 && len > h->graph_chunk) {
+            len = h->graph_chunk;
+            diag = false;
+        }
+        const int rc = run_piece<real, S>(h, len, diag, true);
+        if (rc != LBM_OK) return rc;
+        done += len;
+    }
+    n -= aa;
     long long done = 0;
     while (done < n) {
         long long to_diag = n - done;  // sweeps up to and including the next diagnostic one
@@ -509,6 +573,13 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
         h->rows = kDefaultRows16;
         h->prefetch = kDefaultPrefetch16;
     }
+    // One-buffer streaming where it pays: the FP32 sweep is bound by memory,
+    // and a step whose working set is one buffer finds more of the previous
+    // step's rows in L2 (2048 x 1024 cavity on GB300: 41.4 -> 37.0 us per
+    // step).  The 16-bit sweeps are bound by instruction issue and pay more for
+    // the push sweep's addressing than they gain (BF16-SR 26.4 -> 29.0 us);
+    // FP64 is bound by its arithmetic.
+    h->streaming = precision == LBM_FP32 ? LBM_STREAM_ONE_BUFFER : LBM_STREAM_TWO_BUFFERS;
     set_grid(h);
     h->alloc = g_alloc;
     h->release = g_free;
@@ -683,6 +754,14 @@ int lbm_set_staging(lbm_handle h, int bands) {
     return LBM_OK;
 }
 
+int lbm_set_streaming(lbm_handle h, int mode) {
+    if (!h || (mode != LBM_STREAM_TWO_BUFFERS && mode != LBM_STREAM_ONE_BUFFER))
+        return set_err(h, LBM_ERR_ARG, "mode must be LBM_STREAM_TWO_BUFFERS or LBM_STREAM_ONE_BUFFER");
+    drop_graphs(h);
+    h->streaming = mode;  // between calls buf[cur] always holds the pull layout (phase 0)
+    return LBM_OK;
+}
+
 int lbm_set_wait_limit(lbm_handle h, long long tries, int force_timeout) {
     if (!h || tries < 0 || (force_timeout != 0 && force_timeout != 1))
         return set_err(h, LBM_ERR_ARG, "tries must be >= 0 and force_timeout 0 or 1");
@@ -829,14 +908,15 @@ const char *lbm_version(void) { return "btrirt 0.1 sm_103a"; }
 // Autotuner: picks the launch shape (rows per block, L2 prefetch distance) for
 // a lattice size by timing candidates on a scratch lattice of the same size,
 // precision and parameters, so the caller's state is untouched.  Results are
-// cached per (nx, ny, precision, problem, flow_on) for the process.
+// cached per (nx, ny, precision, problem, flow_on, streaming) for the process.
 // ---------------------------------------------------------------------------
 namespace {
 
 struct TuneKey {
-    int nx, ny, precision, problem, flow;
+    int nx, ny, precision, problem, flow, streaming;
     bool operator==(const TuneKey &o) const {
-        return nx == o.nx && ny == o.ny && precision == o.precision && problem == o.problem && flow == o.flow;
+        return nx == o.nx && ny == o.ny && precision == o.precision && problem == o.problem && flow == o.flow &&
+               streaming == o.streaming;
     }
 };
 struct TuneEntry {
@@ -853,7 +933,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps_per_trial, int *rows_out, in
                             float *us_per_step_out) {
     if (!h || steps_per_trial < 1) return set_err(h, LBM_ERR_ARG, "lbm_autotune: bad argument");
     if (!h->params_set) return set_err(h, LBM_ERR_STATE, "lbm_autotune: parameters not set");
-    const TuneKey key{h->nx, h->ny, h->precision, h->p.problem, h->p.flow_on != 0};
+    const TuneKey key{h->nx, h->ny, h->precision, h->p.problem, h->p.flow_on != 0, h->streaming};
     TuneEntry best{key, h->rows, h->prefetch, 0.0f};
     bool cached = false;
     {
@@ -870,6 +950,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps_per_trial, int *rows_out, in
         int rc = lbm_create(h->nx, h->ny, h->precision, h->stream, &t);
         if (rc != LBM_OK) return set_err(h, rc, "lbm_autotune: scratch lattice: %s", lbm_last_error(nullptr));
         rc = lbm_set_params(t, &h->p);
+        if (rc == LBM_OK) rc = lbm_set_streaming(t, h->streaming);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
             rc = set_err(h, LBM_ERR_CUDA, "lbm_autotune: cudaEventCreate failed");

@@ -16,6 +16,20 @@ enum Mode {
     kFields = 2,     // stream + macroscopic step only: write the fields, no populations
 };
 
+// How populations move from one step to the next.  Pull: two buffers, every
+// sweep pulls f*_i(x - c_i) from src and writes f*_i(x) into its own slot i of
+// dst ("the pull layout": slot i of cell x holds f*_i(x)).  One buffer, two
+// alternating sweeps (src == dst; the AA pattern of Bailey et al. 2009):
+//   push  -- from the pull layout: pull as above, then put f*_i(x) into slot
+//            opp(i) of cell x + c_i, or into the cell's own slot i where
+//            x + c_i lies beyond a wall;
+//   local -- from the pushed layout: f_i(x) is the cell's own slot opp(i) (a
+//            wall's incoming population then takes the wall rule), and f*_i(x)
+//            goes to its own slot i: the pull layout again.
+// Each cell reads and writes the same 18 locations in either sweep, so no two
+// cells touch one location, and the populations are those of the pull sweeps.
+enum Streaming { kPull = 0, kAAPush = 1, kAALocal = 2 };
+
 // Population layout in device memory ("tile-major structure of arrays").
 // The lattice is cut into column tiles of kTW cells.  Within a tile, each row
 // holds the 18 planes (f_0..f_8, g_0..g_8) one after the other, kTW values
@@ -113,7 +127,7 @@ struct BF16;
 // waits for that kernel's completion before it touches memory).
 template <typename real, typename S>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
-                           dim3 grid, dim3 block, cudaStream_t s, bool pdl);
+                           dim3 grid, dim3 block, cudaStream_t s, bool pdl, int streaming = kPull);
 template <typename real, typename S>
 cudaError_t launch_init(const SweepArgs<real> &a, double amp, uint64_t seed, dim3 grid,
                         dim3 block, cudaStream_t s);

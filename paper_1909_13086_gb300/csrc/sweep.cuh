@@ -561,6 +561,49 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
     }
 }
 
+// The local sweep of one-buffer streaming: f_i(x) is the cell's own slot
+// opp(i) -- put there by the neighbour x - c_i's push, or, where x - c_i lies
+// beyond a wall, by the cell's own push of f*_opp(i)(x) -- so a cell takes all
+// its populations from its own tile row (b: its element of plane 0).
+template <typename real, typename S, bool FLOW>
+__device__ __forceinline__ void pull_local(const typename Store<S>::elem *b, real f[9], real g[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        real fv = real(0), gv;
+        load_own<real, S, FLOW>(b, opp_of(i), fv, gv);
+        if (FLOW) f[i] = fv;
+        g[i] = gv;
+    }
+}
+// Wall rules of the local sweep for a cell on the lattice's edge: the slots
+// of wall-crossing directions hold the cell's own f*_opp(i)(x), the value
+// pull_any reads there, and take the same rule (bounce-back as it is;
+// anti-bounce-back on the wall held at T_h, whose inflow enters q).
+template <typename real, typename S, int PROB, bool FLOW>
+__device__ __forceinline__ void wall_rules_local(const SweepArgs<real> &a, int x, int y, real g[9],
+                                                 double &q) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        int sx = x - cx, sy = y - cy;
+        if (PROB == kStefan) sy = (sy < 0) ? sy + a.ny : ((sy >= a.ny) ? sy - a.ny : sy);
+        const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
+        if (in) continue;
+        bool heated;
+        if (PROB == kStefan) {
+            heated = sx < 0;
+        } else {
+            const int xc2 = 2 * x + 1 - cx;  // twice the wall-crossing abscissa
+            heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
+        }
+        if (heated) {
+            const real wt = real(2) * w_of<real>(i) * real(Store<S>::kG);
+            q += (double)((wt - real(2) * g[i]) * (real(1) / real(Store<S>::kG)));
+            g[i] = wt - g[i];
+        }
+    }
+}
+
 // Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel
 // launched with the programmatic-serialization attribute may start while the
 // previous kernel of its stream is still running: each block first lets the
@@ -865,11 +908,54 @@ __device__ __forceinline__ void diag_partial_rows(const CellSums<double> &acc, d
     diag_partial<double>(acc.sfl, acc.sH, acc.umax2, acc.bad, dpart, bid, sh);
 }
 
-// Collide the pulled populations of cell (x, y) and store them at element
-// offset c (cell_index(x, y, 0)) of the destination (MODE == kFields: write
-// the fields instead).
-template <typename real, typename S, bool FLOW, int MODE>
-__device__ __forceinline__ void finish_cell(const SweepArgs<real> &a, int x, int y, long long c, real f[9],
+// Where a cell's post-collision population of direction i goes: cell(i) is
+// the target cell's element of plane 0, slot(i) the direction slot written
+// there.  OwnDst: the cell's own slot i (the pull sweeps, and the local sweep
+// of one-buffer streaming).  PushFast / PushAny: the push sweep of one-buffer
+// streaming (Streaming in lbm_internal.h), slot opp(i) of cell x + c_i, or the
+// cell's own slot i where x + c_i lies beyond a wall.  PushFast serves cells
+// whose eight neighbours all lie inside the lattice: its targets are the
+// base pointers of pull_fast (b, and bL / bR shifted into the neighbouring
+// tile at the tile's first / last column) plus compile-time offsets.
+template <typename S>
+struct OwnDst {
+    typename Store<S>::elem *d;
+    __device__ __forceinline__ typename Store<S>::elem *cell(int) const { return d; }
+    __device__ __forceinline__ int slot(int i) const { return i; }
+};
+template <typename S>
+struct PushFast {
+    typename Store<S>::elem *b, *bL, *bR;
+    __device__ __forceinline__ typename Store<S>::elem *cell(int i) const {
+        const int cx = cx_of(i), cy = cy_of(i);
+        return (cx > 0 ? bR : (cx < 0 ? bL : b)) + cy * kRS + cx * col_step<S>();
+    }
+    __device__ __forceinline__ int slot(int i) const { return opp_of(i); }
+};
+template <typename S, int PROB>
+struct PushAny {
+    typename Store<S>::elem *buf;  // the buffer's first element
+    int x, y, nx, ny;
+    __device__ __forceinline__ bool inside(int i, int &tx, int &ty) const {
+        tx = x + cx_of(i);
+        ty = y + cy_of(i);
+        if (PROB == kStefan) ty = (ty < 0) ? ty + ny : ((ty >= ny) ? ty - ny : ty);  // periodic in y
+        return (unsigned)tx < (unsigned)nx && (unsigned)ty < (unsigned)ny;
+    }
+    __device__ __forceinline__ typename Store<S>::elem *cell(int i) const {
+        int tx, ty;
+        return buf + (inside(i, tx, ty) ? cell_index<S>(tx, ty, 0, ny) : cell_index<S>(x, y, 0, ny));
+    }
+    __device__ __forceinline__ int slot(int i) const {
+        int tx, ty;
+        return inside(i, tx, ty) ? opp_of(i) : i;
+    }
+};
+
+// Collide the streamed populations of cell (x, y) and store them where dst
+// says (MODE == kFields: write the fields instead).
+template <typename real, typename S, bool FLOW, int MODE, typename Dst>
+__device__ __forceinline__ void finish_cell(const SweepArgs<real> &a, int x, int y, const Dst &dst, real f[9],
                                             real g[9], uint32_t step_seed, CellDiag<real> &cd) {
     using E = typename Store<S>::elem;
     if (MODE == kFields) {
@@ -884,30 +970,34 @@ __device__ __forceinline__ void finish_cell(const SweepArgs<real> &a, int x, int
         return;
     }
     const Macro<real> m = cell_update<real, S, FLOW, true>(a, f, g);
-    E *d = static_cast<E *>(a.dst) + c;
     if constexpr (Store<S>::kDev) {
         // paired layout: one 32-bit (g_i, f_i) word per direction; without
         // flow only the g halves are written
-        uint32_t *dw = reinterpret_cast<uint32_t *>(d);
         if (!Store<S>::kSR || (!FLOW && !(isfinite(m.H) && isfinite(m.rho)))) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                if (FLOW) dw[i * kTW] = Store<S>::pack_rn(g[i], f[i]);
-                else Store<S>::str_rn(d + 2 * i * kTW + 1, g[i]);
+                E *d = dst.cell(i);
+                const int s = dst.slot(i);
+                if (FLOW) reinterpret_cast<uint32_t *>(d)[s * kTW] = Store<S>::pack_rn(g[i], f[i]);
+                else Store<S>::str_rn(d + 2 * s * kTW + 1, g[i]);
             }
         } else {
             uint32_t rs = hash32(step_seed ^ (uint32_t)((long long)y * a.nx + x));
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                if (FLOW) dw[i * kTW] = Store<S>::pack_sr(g[i], f[i], lcg_next32(rs));
-                else Store<S>::strs(d + 2 * i * kTW + 1, g[i], lcg_next(rs));
+                E *d = dst.cell(i);
+                const int s = dst.slot(i);
+                if (FLOW) reinterpret_cast<uint32_t *>(d)[s * kTW] = Store<S>::pack_sr(g[i], f[i], lcg_next32(rs));
+                else Store<S>::strs(d + 2 * s * kTW + 1, g[i], lcg_next(rs));
             }
         }
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            Store<S>::str_rn(d + (9 + i) * kTW, g[i]);
-            if (FLOW) Store<S>::str_rn(d + i * kTW, f[i]);
+            E *d = dst.cell(i);
+            const int s = dst.slot(i);
+            Store<S>::str_rn(d + (9 + s) * kTW, g[i]);
+            if (FLOW) Store<S>::str_rn(d + s * kTW, f[i]);
         }
     }
     if (MODE == kSweepDiag) {
@@ -983,7 +1073,9 @@ __device__ __forceinline__ int row_band(const int k, const int gy, const int rev
 // (a.rows rows) of the lattice described by a; gx is the number of tile
 // columns (for the block's partial-sum slot).  Called by lattice_kernel (one
 // lattice, bx = blockIdx.x) and batch_kernel (a block of a batch of lattices).
-template <typename real, typename S, int PROB, bool FLOW, int MODE>
+// SM: kPull, or one of the two sweeps of one-buffer streaming (kAAPush,
+// kAALocal; a.src == a.dst).
+template <typename real, typename S, int PROB, bool FLOW, int MODE, int SM = kPull>
 __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int bx, const int by,
                                             const int gx, double *sh) {
     using E = typename Store<S>::elem;
@@ -1019,18 +1111,36 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
         iR = (lx == kTW - 1 && x < a.nx - 1) ? cell_index<S>(x + 1, y0, 0, a.ny) - cs : i0;
     }
 
+    E *const dst = static_cast<E *>(a.dst);
     CellSums<real> acc;
     for (int y = y0; y < y1; ++y, i0 += kRS, iL += kRS, iR += kRS) {
         CellDiag<real> cd;
         if (active) {
             real f[9], g[9];
-            if ((fastcol || sidewall) && y >= 1 && y <= a.ny - 2) {
+            const bool inner = y >= 1 && y <= a.ny - 2;
+            if (SM == kAALocal) {
+                pull_local<real, S, FLOW>(src + i0, f, g);
+                if (x == 0 || x == a.nx - 1 || (PROB == kCavity && (y == 0 || y == a.ny - 1)))
+                    wall_rules_local<real, S, PROB, FLOW>(a, x, y, g, acc.q);
+            } else if ((fastcol || (SM == kPull && sidewall)) && inner) {
+                // (a side-wall warp's clamped loads read other cells' slots,
+                // which the push sweep may be rewriting: it pulls those warps
+                // with pull_any, which reads only what the cell itself writes)
                 pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
-                if (sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
+                if (SM == kPull && sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
             } else {
                 pull_any<real, S, PROB, FLOW>(a, x, y, f, g, acc.q);
             }
-            finish_cell<real, S, FLOW, MODE>(a, x, y, i0, f, g, step_seed, cd);
+            if (SM == kAAPush) {
+                if (fastcol && inner)
+                    finish_cell<real, S, FLOW, MODE>(a, x, y, PushFast<S>{dst + i0, dst + iL, dst + iR}, f, g,
+                                                     step_seed, cd);
+                else
+                    finish_cell<real, S, FLOW, MODE>(a, x, y, PushAny<S, PROB>{dst, x, y, a.nx, a.ny}, f, g,
+                                                     step_seed, cd);
+            } else {
+                finish_cell<real, S, FLOW, MODE>(a, x, y, OwnDst<S>{dst + i0}, f, g, step_seed, cd);
+            }
         }
         if (MODE == kSweepDiag) diag_row(acc, cd);  // the whole warp, active or not
     }
@@ -1040,14 +1150,15 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
 // FP32 arithmetic: at least 8 blocks of 128 threads per SM (registers capped at
 // 64, the occupancy the memory pipeline needs); FP64 is ALU-bound and keeps its
 // registers.
-template <typename real, typename S, int PROB, bool FLOW, int MODE>
+template <typename real, typename S, int PROB, bool FLOW, int MODE, int SM = kPull>
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     lattice_kernel(const SweepArgs<real> a) {
     __shared__ double sh[32 * 4];
     pdl_launch_dependents();
     pdl_wait();  // the previous sweep's populations, tickets and record
-    sweep_block<real, S, PROB, FLOW, MODE>(a, blockIdx.x, row_band((int)blockIdx.y, (int)gridDim.y, a.parity),
-                                           gridDim.x, sh);
+    sweep_block<real, S, PROB, FLOW, MODE, SM>(a, blockIdx.x,
+                                               row_band((int)blockIdx.y, (int)gridDim.y, a.parity), gridDim.x,
+                                               sh);
 }
 
 // ---- the staged sweep (16-bit storage) ----
@@ -1296,7 +1407,9 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
                 }
             }
         }
-        finish_cell<real, S, FLOW, MODE>(a, x, y, cell_index<S>(x, y, 0, a.ny), f, g, step_seed, cd);
+        finish_cell<real, S, FLOW, MODE>(
+            a, x, y, OwnDst<S>{static_cast<typename Store<S>::elem *>(a.dst) + cell_index<S>(x, y, 0, a.ny)}, f, g,
+            step_seed, cd);
         if (MODE == kSweepDiag) diag_row(acc, cd);
     }
     block_epilogue<real, PROB, MODE>(a, bx, band, gridDim.x, acc, sh);
@@ -1527,7 +1640,23 @@ static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cud
 
 template <typename real, typename S, int PROB, bool FLOW>
 static cudaError_t launch_mode(const SweepArgs<real> &a, int mode, dim3 grid, dim3 block,
-                               cudaStream_t s, bool pdl) {
+                               cudaStream_t s, bool pdl, int streaming) {
+    if (streaming == kAAPush || streaming == kAALocal) {  // one-buffer streaming: sweeps only
+        if (a.src != a.dst || a.staged) return cudaErrorInvalidValue;
+        const bool push = streaming == kAAPush;
+        switch (mode) {
+            case kSweep:
+                return push ? launch_k(lattice_kernel<real, S, PROB, FLOW, kSweep, kAAPush>, grid, block, s, pdl, a)
+                            : launch_k(lattice_kernel<real, S, PROB, FLOW, kSweep, kAALocal>, grid, block, s, pdl, a);
+            case kSweepDiag:
+                return push ? launch_k(lattice_kernel<real, S, PROB, FLOW, kSweepDiag, kAAPush>, grid, block, s, pdl,
+                                       a)
+                            : launch_k(lattice_kernel<real, S, PROB, FLOW, kSweepDiag, kAALocal>, grid, block, s,
+                                       pdl, a);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (streaming != kPull) return cudaErrorInvalidValue;
     if constexpr (Store<S>::kDev) {
         if (a.staged && (mode == kSweep || mode == kSweepDiag)) {
             cudaLaunchConfig_t cfg = {};
@@ -1568,14 +1697,14 @@ static cudaError_t launch_diag_reduce(const SweepArgs<real> &a, dim3 grid, bool 
 
 template <typename real, typename S>
 cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int mode,
-                           dim3 grid, dim3 block, cudaStream_t s, bool pdl) {
+                           dim3 grid, dim3 block, cudaStream_t s, bool pdl, int streaming) {
     cudaError_t e;
     if (problem == kCavity)
-        e = flow ? launch_mode<real, S, kCavity, true>(a, mode, grid, block, s, pdl)
-                 : launch_mode<real, S, kCavity, false>(a, mode, grid, block, s, pdl);
+        e = flow ? launch_mode<real, S, kCavity, true>(a, mode, grid, block, s, pdl, streaming)
+                 : launch_mode<real, S, kCavity, false>(a, mode, grid, block, s, pdl, streaming);
     else
-        e = flow ? launch_mode<real, S, kStefan, true>(a, mode, grid, block, s, pdl)
-                 : launch_mode<real, S, kStefan, false>(a, mode, grid, block, s, pdl);
+        e = flow ? launch_mode<real, S, kStefan, true>(a, mode, grid, block, s, pdl, streaming)
+                 : launch_mode<real, S, kStefan, false>(a, mode, grid, block, s, pdl, streaming);
     if (e == cudaSuccess && mode == kSweepDiag) e = launch_diag_reduce(a, grid, false, s, pdl);
     return e;
 }
@@ -1634,7 +1763,7 @@ cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, 
 // Explicit instantiation of every launcher for one (compute, storage) pair.
 #define BTRIRT_INSTANTIATE(REAL, S)                                                             \
     template cudaError_t launch_lattice<REAL, S>(const SweepArgs<REAL> &, int, bool, int, dim3,  \
-                                                 dim3, cudaStream_t, bool);                      \
+                                                 dim3, cudaStream_t, bool, int);                 \
     template cudaError_t launch_init<REAL, S>(const SweepArgs<REAL> &, double, uint64_t, dim3,   \
                                               dim3, cudaStream_t);                               \
     template cudaError_t launch_fields0<REAL, S>(const SweepArgs<REAL> &, bool, dim3, dim3,      \

@@ -23,6 +23,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE,
     0, -1, -2, -3, -4, -5, -6
 LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16, LBM_FP16_SR, LBM_BF16_SR = 0, 1, 2, 3, 4, 5
 LBM_CAVITY, LBM_STEFAN = 0, 1
+LBM_STREAM_TWO_BUFFERS, LBM_STREAM_ONE_BUFFER = 0, 1
 FIELD_BITS = {"H": 1, "T": 2, "fl": 4, "ux": 8, "uy": 16, "rho": 32}
 FIELD_NAMES = ("H", "T", "fl", "ux", "uy", "rho")
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16,
@@ -68,7 +69,7 @@ class lbm_launch_stats(ctypes.Structure):
 
 
 EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_set_diag_every",
-            "lbm_set_launch", "lbm_get_launch_stats", "lbm_set_staging", "lbm_set_wait_limit",
+            "lbm_set_launch", "lbm_get_launch_stats", "lbm_set_staging", "lbm_set_streaming", "lbm_set_wait_limit",
             "lbm_read_fields", "lbm_diagnostics", "lbm_read_populations", "lbm_write_populations",
             "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
@@ -99,6 +100,7 @@ def lib() -> ctypes.CDLL:
     L.lbm_set_launch.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.lbm_get_launch_stats.argtypes = [H, ctypes.POINTER(lbm_launch_stats)]
     L.lbm_set_staging.argtypes = [H, ctypes.c_int]
+    L.lbm_set_streaming.argtypes = [H, ctypes.c_int]
     L.lbm_set_wait_limit.argtypes = [H, ctypes.c_longlong, ctypes.c_int]
     L.lbm_read_fields.argtypes = [H, ctypes.c_uint] + [_D] * 6
     L.lbm_diagnostics.argtypes = [H, ctypes.POINTER(lbm_diag)]
@@ -192,6 +194,10 @@ def lbm_set_launch(h, rows: int = 1, prefetch: int = 16, graph_chunk: int = 128)
 
 def lbm_set_staging(h, bands: int = -1) -> None:
     _check(lib().lbm_set_staging(h, int(bands)), h)
+
+
+def lbm_set_streaming(h, mode: int = LBM_STREAM_ONE_BUFFER) -> None:
+    _check(lib().lbm_set_streaming(h, int(mode)), h)
 
 
 def lbm_set_wait_limit(h, tries: int = 1 << 20, force_timeout: bool = False) -> None:

@@ -109,3 +109,72 @@ def test_paired_layout_is_a_permutation_of_the_tile_row():
         for lx in range(TW):
             f, g = plane_ofs(i, lx, True), plane_ofs(9 + i, lx, True)
             assert f % 2 == 0 and g == f + 1
+
+
+# ---- one-buffer streaming (the push sweep): every cell must read and write
+# the same locations, and no location may be written by two cells --------------
+OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+
+
+def elem(x, y, plane, ny, paired):
+    return pop_index(x, y, plane, ny, paired)
+
+
+def push_sweep_sets(nx, ny, paired, stefan, flow):
+    """Per cell, the elements the push sweep reads and writes, replaying the
+    sweep's own arithmetic: pull_fast's bases and offsets and PushFast's
+    targets (base by c_x, + c_y rows + c_x columns, slot opp(i)) for cells of
+    warps clear of both side walls on interior rows; pull_any's and PushAny's
+    per-direction targets elsewhere (y periodic for the Stefan problem)."""
+    cs = 2 if paired else 1
+    halves = (0, 9) if flow else (9,)
+    offs = load_offsets(paired)
+    out = {}
+    for x in range(nx):
+        bx, lx = divmod(x, TW)
+        xw = bx * TW + (lx // 32) * 32
+        fastcol = xw >= 1 and xw + 31 <= nx - 2
+        for y in range(ny):
+            inner = 1 <= y <= ny - 2
+            reads, writes = [], []
+            if fastcol and inner:
+                i0 = pop_index(x, y, 0, ny, paired)
+                iL = pop_index(x - 1, y, 0, ny, paired) + cs if lx == 0 else i0
+                iR = pop_index(x + 1, y, 0, ny, paired) - cs if lx == TW - 1 else i0
+                bases = (i0, iL, iR)
+                for base, off, plane, cx, cy in offs:
+                    if plane >= 9 or flow:
+                        reads.append(bases[base] + off)
+                for i, (cx, cy) in enumerate(C):
+                    d = (iR if cx > 0 else (iL if cx < 0 else i0)) + cy * RS + cx * cs
+                    for P in halves:
+                        e = d + (2 * OPP[i] * TW + (1 if P else 0) if paired else (P + OPP[i]) * TW)
+                        assert e == elem(x + cx, y + cy, P + OPP[i], ny, paired), (nx, x, y, i, P)
+                        writes.append(e)
+            else:
+                for i, (cx, cy) in enumerate(C):
+                    sx, sy, tx, ty = x - cx, y - cy, x + cx, y + cy
+                    if stefan:
+                        sy, ty = sy % ny, ty % ny
+                    src_in = 0 <= sx < nx and 0 <= sy < ny
+                    dst_in = 0 <= tx < nx and 0 <= ty < ny
+                    for P in halves:
+                        reads.append(elem(sx, sy, P + i, ny, paired) if src_in else elem(x, y, P + OPP[i], ny, paired))
+                        writes.append(elem(tx, ty, P + OPP[i], ny, paired) if dst_in else elem(x, y, P + i, ny, paired))
+            out[(x, y)] = (reads, writes)
+    return out
+
+
+@pytest.mark.parametrize("paired", [False, True])
+@pytest.mark.parametrize("stefan,flow", [(False, True), (False, False), (True, False), (True, True)])
+@pytest.mark.parametrize("nx,ny", [(2, 3), (3, 4), (33, 5), (127, 3), (128, 4), (129, 6), (256, 3), (300, 7)])
+def test_push_sweep_reads_what_it_writes(nx, ny, paired, stefan, flow):
+    total = ((nx + TW - 1) // TW) * ny * RS
+    seen = set()
+    for (x, y), (reads, writes) in push_sweep_sets(nx, ny, paired, stefan, flow).items():
+        assert len(set(writes)) == len(writes) == len(reads), (x, y)
+        assert set(reads) == set(writes), (nx, ny, x, y)
+        for w in writes:
+            assert 0 <= w < total
+            assert w not in seen, (nx, ny, x, y, w)   # no location written by two cells
+            seen.add(w)
