@@ -192,7 +192,8 @@ int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int grap
  * and checkpoints do not depend on the mode, bit for bit.  One buffer halves
  * the working set of a step, so that more of what the previous step wrote is
  * still in L2 when the next one reads it.  Both buffers stay allocated.  The
- * staged 16-bit sweep, batches and lbm_step_static always use two buffers.
+ * staged 16-bit sweep and lbm_step_static always use two buffers; a batch has
+ * its own setting (lbm_batch_set_streaming).
  * Default (set by lbm_create): one buffer for LBM_FP32, whose sweep is bound
  * by memory (2048 x 1024 cavity on GB300: 41.4 -> 37.0 us per step); two
  * buffers for the 16-bit types, whose sweeps are bound by instruction issue
@@ -345,6 +346,17 @@ int lbm_batch_step(lbm_batch b, long long n);
  * by member).  Results do not depend on it.  Takes effect at the next
  * lbm_batch_step.  Errors: LBM_ERR_ARG. */
 int lbm_batch_set_launch(lbm_batch b, int rows_per_block, int prefetch_rows, int interleave);
+
+/* Streaming of the batch's step kernel, as lbm_set_streaming for one lattice:
+ * with LBM_STREAM_ONE_BUFFER all but the last one or two steps of an
+ * lbm_batch_step call alternate push and local sweeps in each member's current
+ * buffer, and the closing steps run over two buffers, so that between calls
+ * every member's state is the two-buffer one (results do not depend on the
+ * mode, bit for bit; members may be stepped alone or in other batches between
+ * calls).  Until this is called the batch follows its precision: one buffer for
+ * LBM_FP32, two otherwise.  Synchronises the batch's stream.  Errors:
+ * LBM_ERR_ARG. */
+int lbm_batch_set_streaming(lbm_batch b, int mode);
 
 /* Autotuner for a batch: times rows per block (1, 2, 3, 4) x prefetch distance
  * (0, 4, 8, 16 rows) x block order (member by

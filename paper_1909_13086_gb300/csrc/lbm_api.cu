@@ -1018,6 +1018,7 @@ struct lbm_batch_s {
     int rows = 0;             // launch shape: rows per block (0: 2, or 4 with 16-bit storage),
     int prefetch = -1;        // L2 prefetch distance (-1: 4 rows),
     int interleave = 1;       // interleaved block order (uniform batches only; see batch_kernel)
+    int streaming = -1;       // lbm_batch_set_streaming; -1: one buffer for FP32, two otherwise
     bool dirty = true;        // table must be rebuilt and uploaded
     int precision = -1, problem = -1, flow = -1;
     int graph_chunk = 128;    // longest graph-replayed piece; even, so that every
@@ -1129,26 +1130,34 @@ int batch_steps(lbm_batch_s *b, long long n) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     BATCH_TRY(cudaStreamIsCapturing(b->stream, &st));
     const bool capturing = st != cudaStreamCaptureStatusNone;
-    auto direct = [&](long long from, long long len, bool diag) -> int {
+    // One-buffer streaming (lbm_batch_set_streaming): the first sweeps of the
+    // call, an even number, alternate push (even j) and local (odd j) sweeps
+    // in each member's buffer parity[r]; the last one or two run over the two
+    // buffers, so that between calls every member's state is the two-buffer one.
+    const bool one = b->streaming < 0 ? b->precision == LBM_FP32 : b->streaming == LBM_STREAM_ONE_BUFFER;
+    const long long aa = (one && n >= 3) ? ((n & 1) ? n - 1 : n - 2) : 0;
+    auto direct = [&](long long from, long long len, bool diag, bool ob) -> int {
         for (long long j = 0; j < len; ++j) {
+            const long long jj = from + j;
+            const int sm = ob ? ((jj & 1) ? kAALocal : kAAPush) : kPull;
             const cudaError_t e = launch_batch<real, S>(b->entries, b->starts, b->parity, nm, b->uniform,
                                                         b->uniform > 0 ? b->interleave : 0, b->nblocks,
                                                         b->problem, b->flow != 0,
-                                                        diag && j == len - 1, (int)((from + j) & 1),
-                                                        b->stream, true);
+                                                        diag && j == len - 1, (int)(jj & 1),
+                                                        b->stream, true, sm);
             if (e != cudaSuccess) return batch_err(LBM_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
         }
         return LBM_OK;
     };
-    while (done < n) {
-        const bool full = K >= 2 && n - done > K;
-        const long long len = full ? K : n - done;
-        const bool diag = !full;
+    // One piece, starting at an even step `from` of the call: launched
+    // directly the first time it is asked for, captured the second time,
+    // replayed from then on.
+    auto piece = [&](long long from, long long len, bool diag, bool ob) -> int {
         ChunkGraph *slot = nullptr;
         const bool graphs = K >= 2 && len >= 2 && len <= K && !capturing;
         if (graphs) {
             for (ChunkGraph &g : b->graphs)
-                if (g.used && g.len == len && g.diag == diag) slot = &g;
+                if (g.used && g.len == len && g.diag == diag && g.one_buffer == ob) slot = &g;
             if (!slot) {
                 ChunkGraph *victim = &b->graphs[0];
                 for (ChunkGraph &g : b->graphs) {
@@ -1160,10 +1169,11 @@ int batch_steps(lbm_batch_s *b, long long n) {
                 victim->used = true;
                 victim->len = (int)len;
                 victim->diag = diag;
+                victim->one_buffer = ob;
                 victim->stamp = ++b->graph_clock;
             } else if (!slot->exec) {
                 BATCH_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-                const int rc = direct(0, len, diag);
+                const int rc = direct(0, len, diag, ob);
                 cudaGraph_t g = nullptr;
                 const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
                 if (rc != LBM_OK || e2 != cudaSuccess) {
@@ -1183,10 +1193,21 @@ int batch_steps(lbm_batch_s *b, long long n) {
         if (slot && slot->exec) {
             slot->stamp = ++b->graph_clock;
             BATCH_TRY(cudaGraphLaunch(slot->exec, b->stream));
-        } else {
-            const int rc = direct(done, len, diag);
-            if (rc != LBM_OK) return rc;
+            return LBM_OK;
         }
+        return direct(from, len, diag, ob);
+    };
+    while (done < aa) {  // K and aa are even: every piece starts at an even step
+        const long long len = (K >= 2 && aa - done > K) ? K : aa - done;
+        const int rc = piece(done, len, false, true);
+        if (rc != LBM_OK) return rc;
+        done += len;
+    }
+    while (done < n) {
+        const bool full = K >= 2 && n - done > K;
+        const long long len = full ? K : n - done;
+        const int rc = piece(done, len, !full, false);
+        if (rc != LBM_OK) return rc;
         done += len;
     }
     for (lbm_s *h : b->members) {
@@ -1326,6 +1347,16 @@ int lbm_batch_set_launch(lbm_batch b, int rows_per_block, int prefetch_rows, int
     return LBM_OK;
 }
 
+int lbm_batch_set_streaming(lbm_batch b, int mode) {
+    if (!b || (mode != LBM_STREAM_TWO_BUFFERS && mode != LBM_STREAM_ONE_BUFFER))
+        return batch_err(LBM_ERR_ARG,
+                         "lbm_batch_set_streaming: mode must be LBM_STREAM_TWO_BUFFERS or LBM_STREAM_ONE_BUFFER");
+    if (b->stream) cudaStreamSynchronize(b->stream);  // no captured piece may be in flight
+    batch_drop_graph(b);
+    b->streaming = mode;
+    return LBM_OK;
+}
+
 int lbm_batch_destroy(lbm_batch b) {
     if (!b) return LBM_OK;
     DeviceGuard g(b->device);
@@ -1356,10 +1387,11 @@ struct BatchTune {
 std::mutex g_btune_mutex;
 std::vector<BatchTune> g_btune_cache;
 
-// The composition: precision, problem, flow, then every member's size in order.
+// The composition: precision, problem, flow, streaming, then every member's
+// size in order.
 std::string batch_key(const lbm_batch_s *b) {
     std::string k = std::to_string(b->precision) + "/" + std::to_string(b->problem) + "/" +
-                    std::to_string(b->flow);
+                    std::to_string(b->flow) + "/" + std::to_string(b->streaming);
     for (const lbm_s *h : b->members) k += "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny);
     return k;
 }
@@ -1388,6 +1420,7 @@ extern "C" int lbm_batch_autotune(lbm_batch b, int steps_per_trial, int *rows_ou
         std::vector<lbm_handle> scratch;
         lbm_batch t = nullptr;
         int rc = lbm_batch_create((int)b->members.size(), b->stream, &t);
+        if (rc == LBM_OK) t->streaming = b->streaming;
         for (size_t r = 0; r < b->members.size() && rc == LBM_OK; ++r) {
             const lbm_s *h = b->members[r];
             lbm_handle s = nullptr;

@@ -150,11 +150,13 @@ struct BatchEntry {
 // parity[r] is entry r's source buffer at step j = 0; uniform > 0 when every
 // entry has that many blocks (0 otherwise); interleave (uniform batches only):
 // block b belongs to entry b mod n instead of b / uniform.  diag: diagnostic
-// sweep plus the per-entry fold.
+// sweep plus the per-entry fold.  streaming: kPull (buffer parity[r] ^ (j & 1)
+// into the other), or the push (even j) / local (odd j) sweep of one-buffer
+// streaming in buffer parity[r].
 template <typename real, typename S>
 cudaError_t launch_batch(const void *entries, const int *starts, const int *parity, int n,
                          int uniform, int interleave, int nblocks, int problem, bool flow, bool diag,
-                         int j, cudaStream_t s, bool pdl);
+                         int j, cudaStream_t s, bool pdl, int streaming = kPull);
 // Tile-major buffer <-> plane-major FP64 staging (18 planes of nx*ny, f then g).
 // to_staging = true packs buf into stage; false unpacks stage into buf (and,
 // if buf2 is non-NULL, the f planes into buf2 as well).  Values in the staging

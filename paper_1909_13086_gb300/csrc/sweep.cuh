@@ -1438,7 +1438,11 @@ __device__ __forceinline__ int batch_find(const int *starts, int n, int b) {
     return lo;
 }
 
-template <typename real, typename S, int PROB, bool FLOW, int MODE>
+// SM: kPull, or a sweep of one-buffer streaming (kAAPush at even j, kAALocal
+// at odd j): the member's arguments for its buffer parity[r] are then used
+// with the destination set to the source and the parity word to
+// parity[r] ^ (j & 1), patched in the shared-memory copy.
+template <typename real, typename S, int PROB, bool FLOW, int MODE, int SM = kPull>
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     batch_kernel(const BatchEntry<real> *entries, const int *starts, const int *parity, int n,
                  int uniform, int interleave, int j) {
@@ -1463,12 +1467,21 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     int4 *d4 = reinterpret_cast<int4 *>(entry_sh);
     for (unsigned k = threadIdx.x; k < sizeof(BatchEntry<real>) / 16; k += blockDim.x)
         d4[k] = __ldg(s4 + k);
-    if (threadIdx.x == 0) meta[1] = __ldg(parity + r) ^ (j & 1);
+    if (threadIdx.x == 0) meta[1] = __ldg(parity + r) ^ (SM == kPull ? (j & 1) : 0);
     __syncthreads();
+    if constexpr (SM != kPull) {
+        if (threadIdx.x == 0) {
+            SweepArgs<real> &x = reinterpret_cast<BatchEntry<real> *>(entry_sh)->a[meta[1]];
+            x.dst = const_cast<void *>(x.src);
+            x.parity = meta[1] ^ (j & 1);
+        }
+        __syncthreads();
+    }
     pdl_wait();
     const BatchEntry<real> &e = *reinterpret_cast<const BatchEntry<real> *>(entry_sh);
+    const SweepArgs<real> &a = e.a[meta[1]];
     const int l = (uniform > 0 && interleave) ? (int)(blockIdx.x / (unsigned)n) : (int)blockIdx.x - e.start;
-    sweep_block<real, S, PROB, FLOW, MODE>(e.a[meta[1]], l % e.gx, row_band(l / e.gx, e.gy, meta[1]), e.gx, sh);
+    sweep_block<real, S, PROB, FLOW, MODE, SM>(a, l % e.gx, row_band(l / e.gx, e.gy, a.parity), e.gx, sh);
 }
 
 // Per-entry diagnostics fold after a diagnostic batch step: block r folds the
@@ -1712,21 +1725,31 @@ cudaError_t launch_lattice(const SweepArgs<real> &a, int problem, bool flow, int
 template <typename real, typename S>
 cudaError_t launch_batch(const void *entries, const int *starts, const int *parity, int n,
                          int uniform, int interleave, int nblocks, int problem, bool flow, bool diag,
-                         int j, cudaStream_t s, bool pdl) {
+                         int j, cudaStream_t s, bool pdl, int streaming) {
     const BatchEntry<real> *e = static_cast<const BatchEntry<real> *>(entries);
     const dim3 grid(nblocks), block(kTW);
     cudaError_t err;
-#define BTRIRT_BATCH(PROB, FLOW)                                                                   \
-    err = diag ? launch_k(batch_kernel<real, S, PROB, FLOW, kSweepDiag>, grid, block, s, pdl, e,   \
-                          starts, parity, n, uniform, interleave, j)                               \
-               : launch_k(batch_kernel<real, S, PROB, FLOW, kSweep>, grid, block, s, pdl, e, starts, \
+    if (streaming != kPull && streaming != kAAPush && streaming != kAALocal) return cudaErrorInvalidValue;
+#define BTRIRT_BATCH_SM(PROB, FLOW, SM)                                                                \
+    err = diag ? launch_k(batch_kernel<real, S, PROB, FLOW, kSweepDiag, SM>, grid, block, s, pdl, e, starts, \
+                          parity, n, uniform, interleave, j)                                           \
+               : launch_k(batch_kernel<real, S, PROB, FLOW, kSweep, SM>, grid, block, s, pdl, e, starts,  \
                           parity, n, uniform, interleave, j);
+#define BTRIRT_BATCH(PROB, FLOW)                                                                   \
+    if (streaming == kAAPush) {                                                                    \
+        BTRIRT_BATCH_SM(PROB, FLOW, kAAPush)                                                       \
+    } else if (streaming == kAALocal) {                                                            \
+        BTRIRT_BATCH_SM(PROB, FLOW, kAALocal)                                                      \
+    } else {                                                                                       \
+        BTRIRT_BATCH_SM(PROB, FLOW, kPull)                                                         \
+    }
     if (problem == kCavity) {
         if (flow) { BTRIRT_BATCH(kCavity, true) } else { BTRIRT_BATCH(kCavity, false) }
     } else {
         if (flow) { BTRIRT_BATCH(kStefan, true) } else { BTRIRT_BATCH(kStefan, false) }
     }
 #undef BTRIRT_BATCH
+#undef BTRIRT_BATCH_SM
     if (err == cudaSuccess && diag)
         err = launch_k(batch_diag_reduce_kernel<real, typename DiagAcc<real>::T>, dim3(n),
                        dim3(kReduceThreads), s, pdl, e);
@@ -1770,6 +1793,6 @@ cudaError_t launch_repack(void *buf, void *buf2, double *stage, int nx, int ny, 
                                                  cudaStream_t);                                  \
     template cudaError_t launch_repack<S>(void *, void *, double *, int, int, bool, cudaStream_t); \
     template cudaError_t launch_batch<REAL, S>(const void *, const int *, const int *, int, int,  \
-                                               int, int, int, bool, bool, int, cudaStream_t, bool);
+                                               int, int, int, bool, bool, int, cudaStream_t, bool, int);
 
 }  // namespace btrirt

@@ -74,7 +74,7 @@ EXPORTED = ("lbm_create", "lbm_set_params", "lbm_get_derived", "lbm_step", "lbm_
             "lbm_destroy", "lbm_last_error", "lbm_set_allocator", "lbm_version", "lbm_step_static",
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_count",
             "lbm_batch_step", "lbm_batch_destroy", "lbm_autotune", "lbm_set_history",
-            "lbm_read_history", "lbm_batch_set_launch", "lbm_batch_autotune")
+            "lbm_read_history", "lbm_batch_set_launch", "lbm_batch_set_streaming", "lbm_batch_autotune")
 
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
     L.lbm_get_launch_stats.argtypes = [H, ctypes.POINTER(lbm_launch_stats)]
     L.lbm_set_staging.argtypes = [H, ctypes.c_int]
     L.lbm_set_streaming.argtypes = [H, ctypes.c_int]
+    L.lbm_batch_set_streaming.argtypes = [H, ctypes.c_int]
     L.lbm_set_wait_limit.argtypes = [H, ctypes.c_longlong, ctypes.c_int]
     L.lbm_read_fields.argtypes = [H, ctypes.c_uint] + [_D] * 6
     L.lbm_diagnostics.argtypes = [H, ctypes.POINTER(lbm_diag)]
@@ -293,6 +294,10 @@ def lbm_batch_step(b, n: int) -> None:
 
 def lbm_batch_set_launch(b, rows: int = 0, prefetch: int = -1, interleave: int = 0) -> None:
     _check(lib().lbm_batch_set_launch(b, int(rows), int(prefetch), int(interleave)))
+
+
+def lbm_batch_set_streaming(b, mode: int = LBM_STREAM_ONE_BUFFER) -> None:
+    _check(lib().lbm_batch_set_streaming(b, int(mode)))
 
 
 def lbm_batch_autotune(b, steps_per_trial: int = 50) -> dict:

@@ -130,3 +130,44 @@ def test_bad_mode(stream):
     lat = lbm.Lattice(64, 32, workloads.params(), precision="fp32", stream=stream)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_set_streaming(lat.h, 2)
+
+
+BATCH = [(256, 128, dict(Ra=1e6, strip_center=0.2)), (300, 77, dict(Ra=1e5, strip_center=0.65)),
+         (64, 32, dict()), (130, 9, dict(Ra=1e7, strip_center=0.5, strip_width=0.4, seed=9))]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16sr", "fp64"])
+@pytest.mark.parametrize("shape", [(0, -1, 1), (1, 0, 0), (3, 8, 1), (4, 2, 0)])
+def test_batch_one_buffer_equals_two_buffers(stream, prec, shape):
+    """Mixed sizes, one member a step ahead (its buffer parity differs from the
+    others'), calls of odd and even length; the uniform-size case with the
+    interleaved block order as well."""
+    rows, pf, il = shape
+    out = []
+    for mode in (TWO, ONE):
+        lats = [lbm.Lattice(nx, ny, workloads.params(**kw), precision=prec, stream=stream)
+                for nx, ny, kw in BATCH]
+        lats[1].step(1)
+        same = [lbm.Lattice(128, 64, workloads.params(Ra=1e6, strip_center=c, seed=k), precision=prec,
+                            stream=stream) for k, c in enumerate((0.2, 0.5, 0.8))]
+        res = []
+        for group in (lats, same):
+            b = lbm.Batch(8, stream)
+            for lat in group:
+                b.add(lat)
+            lbm.lbm_batch_set_streaming(b.b, mode)
+            lbm.lbm_batch_set_launch(b.b, rows, pf, il)
+            for n in (150, 37, 2, 1, 150, 37):  # pieces direct, then replayed
+                b.step(n)
+            b.close()
+            res += [state(lat) for lat in group]
+        out.append(res)
+    for k, (a, b_) in enumerate(zip(*out)):
+        assert_same(a, b_, (prec, shape, k))
+
+
+def test_batch_bad_mode(stream):
+    b = lbm.Batch(2, stream)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_set_streaming(b.b, 3)
+    b.close()
