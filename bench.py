@@ -559,6 +559,8 @@ def run_batch(args) -> None:
         "config": {"workload": f"batch of {n} cavities {BATCH_NX}x{BATCH_NY} (Ra 1e6-1e8, strip "
                                f"W/4 at 0.2-0.8 W, seeded), {prec.upper()} populations, one fused "
                                "launch per step", "lattices": n, "precision": prec,
+                   "streaming": ("one buffer (push / local sweeps), the call's last 1-2 steps over two buffers"
+                                 if prec == "fp32" else "two buffers"),
                    # both population buffers together are the algorithmic bytes of a step
                    "l2": (f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB of populations), no flush"
                           if alg_bytes > 129e6 else
