@@ -525,6 +525,28 @@ __device__ __forceinline__ void bounce_side_walls(const typename Store<S>::elem 
     }
 }
 
+// The rule for the g population of direction i entering cell x from beyond a
+// wall (source (sx, sy) outside the lattice), given gv = the cell's own
+// post-collision g*_opp(i): half-way bounce-back (gv as it is) on adiabatic
+// walls; anti-bounce-back 2 w_i C_p T_h - gv on the wall held at T_h (the
+// Stefan problem's left wall, the cavity's heated bottom segment), whose
+// inflow 2 w_i T_h - 2 gv enters q.  Values in g's stored units; q physical.
+template <typename real, typename S, int PROB>
+__device__ __forceinline__ real wall_rule_g(const SweepArgs<real> &a, int x, int i, int sx, int sy, real gv,
+                                            double &q) {
+    bool heated;
+    if (PROB == kStefan) {
+        heated = sx < 0;
+    } else {
+        const int xc2 = 2 * x + 1 - cx_of(i);  // twice the wall-crossing abscissa
+        heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
+    }
+    if (!heated) return gv;
+    const real wt = real(2) * w_of<real>(i) * real(Store<S>::kG);  // 2 w_i C_p T_h, T_h = 1
+    q += (double)((wt - real(2) * gv) * (real(1) / real(Store<S>::kG)));
+    return wt - gv;
+}
+
 // Any cell: explicit source test per direction and the wall rules.
 template <typename real, typename S, int PROB, bool FLOW>
 __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y, real f[9],
@@ -542,21 +564,7 @@ __device__ __forceinline__ void pull_any(const SweepArgs<real> &a, int x, int y,
         real gv, fv = real(0);
         load_own<real, S, FLOW>(src + cell, pl, fv, gv);
         if (FLOW) f[i] = fv;
-        if (!in) {
-            bool heated;
-            if (PROB == kStefan) {
-                heated = sx < 0;
-            } else {
-                const int xc2 = 2 * x + 1 - cx;  // twice the wall-crossing abscissa
-                heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
-            }
-            if (heated) {
-                // 2 w_i C_p T_h (T_h = 1), in g's stored units; q is physical
-                const real wt = real(2) * w_of<real>(i) * real(Store<S>::kG);
-                q += (double)((wt - real(2) * gv) * (real(1) / real(Store<S>::kG)));
-                gv = wt - gv;
-            }
-        }
+        if (!in) gv = wall_rule_g<real, S, PROB>(a, x, i, sx, sy, gv, q);
         g[i] = gv;
     }
 }
@@ -588,19 +596,7 @@ __device__ __forceinline__ void wall_rules_local(const SweepArgs<real> &a, int x
         int sx = x - cx, sy = y - cy;
         if (PROB == kStefan) sy = (sy < 0) ? sy + a.ny : ((sy >= a.ny) ? sy - a.ny : sy);
         const bool in = (unsigned)sx < (unsigned)a.nx && (unsigned)sy < (unsigned)a.ny;
-        if (in) continue;
-        bool heated;
-        if (PROB == kStefan) {
-            heated = sx < 0;
-        } else {
-            const int xc2 = 2 * x + 1 - cx;  // twice the wall-crossing abscissa
-            heated = a.strip_on && sy < 0 && xc2 >= a.lo2 && xc2 <= a.hi2;
-        }
-        if (heated) {
-            const real wt = real(2) * w_of<real>(i) * real(Store<S>::kG);
-            q += (double)((wt - real(2) * g[i]) * (real(1) / real(Store<S>::kG)));
-            g[i] = wt - g[i];
-        }
+        if (!in) g[i] = wall_rule_g<real, S, PROB>(a, x, i, sx, sy, g[i], q);
     }
 }
 
@@ -1058,8 +1054,8 @@ __device__ __forceinline__ void block_epilogue(const SweepArgs<real> &a, int bx,
 // gy bands) works on.  Successive steps visit the interior bands in opposite
 // directions (rev = 1: descending; the source buffer's parity alternates with
 // the step), so that a step starts on the rows the previous step wrote last,
-// which are still in L2: the two population buffers of a large lattice exceed
-// L2, and a sweep in a fixed direction would start on rows long evicted.  The
+// which are still in L2: the populations of a large lattice exceed L2, and a
+// sweep in a fixed direction would start on rows long evicted.  The
 // two wall bands (boundary pulls; the bottom one also folds the heated-wall
 // inflow in the cavity) go first in both directions, so that they do not form
 // the launch's tail.  A permutation of 0 .. gy - 1 for either direction.
