@@ -73,4 +73,14 @@ def test_argument_errors_need_no_gpu(built):
     assert L.lbm_create(8, 65536, 1, None, ctypes.byref(h)) == built.LBM_ERR_ARG   # ny > 65535
     assert L.lbm_create(65536, 40000, 1, None, ctypes.byref(h)) == built.LBM_ERR_ARG  # > 2^31 cells
     assert L.lbm_step(None, 1) == built.LBM_ERR_ARG
+    assert L.lbm_set_streaming(None, built.LBM_STREAM_ONE_BUFFER) == built.LBM_ERR_ARG
+    assert L.lbm_batch_set_streaming(None, built.LBM_STREAM_TWO_BUFFERS) == built.LBM_ERR_ARG
     assert L.lbm_destroy(None) == built.LBM_OK
+
+
+def test_streaming_constants_match_header(built):
+    import re
+
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    m = re.search(r"enum \{ LBM_STREAM_TWO_BUFFERS = (\d+), LBM_STREAM_ONE_BUFFER = (\d+) \};", text)
+    assert m and (int(m.group(1)), int(m.group(2))) == (built.LBM_STREAM_TWO_BUFFERS, built.LBM_STREAM_ONE_BUFFER)
