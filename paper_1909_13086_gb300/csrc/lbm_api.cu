@@ -656,6 +656,7 @@ int lbm_set_params(lbm_handle h, const lbm_params *p) {
     set_grid(h);
     h->step = 0;
     h->cur = 0;
+    h->phase = 0;  // a call cut short mid-way through its one-buffer sweeps may have left 1
     h->has_prev = false;
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned), h->stream));
@@ -807,6 +808,7 @@ int lbm_write_populations(lbm_handle h, const double *f, const double *g, long l
     if (rc != LBM_OK) return rc;
     h->step = step;
     h->has_prev = false;
+    h->phase = 0;  // the buffer now holds the pull layout
     CUDA_TRY(h, cudaMemsetAsync(h->rec, 0, sizeof(DevRecord), h->stream));
     // both tickets back to zero (a sweep cut short by a timeout may leave one taken)
     CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned), h->stream));
