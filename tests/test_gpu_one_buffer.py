@@ -171,3 +171,15 @@ def test_batch_bad_mode(stream):
     with pytest.raises(lbm.LbmError):
         lbm.lbm_batch_set_streaming(b.b, 3)
     b.close()
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(2, 65535, 4), (262144, 2, 4), (129, 65535, 3)])
+def test_extreme_shapes(stream, nx, ny, steps):
+    """The tallest lattice the launch allows, a 2,048-tile strip and a ragged
+    two-tile width at full height: the push sweep's targets across tile and
+    wall edges at every size, against two-buffer streaming (FP32, bitwise)."""
+    p = workloads.params(Ra=1e5, init_amp=0.1)
+    ref, lat = pair(stream, nx, ny, p, "fp32", diag_every=0)
+    ref.step(steps)
+    lat.step(steps)
+    assert_same(state(ref), state(lat), (nx, ny))
