@@ -159,9 +159,13 @@ int lbm_set_diag_every(lbm_handle h, long long k);
  *
  * How lbm_step enqueues its n sweeps: it cuts them into pieces that end at
  * the diagnostic sweeps (every diag_every-th step and the call's last one)
- * and are at most graph_chunk long.  A piece is identified by its length,
- * whether it ends with a diagnostic sweep, and the buffer parity it starts
- * from.  The first time a piece is asked for its sweeps are launched
+ * and are at most graph_chunk long (with one-buffer streaming, see
+ * lbm_set_streaming, the call's one-buffer sweeps are cut the same way, ending
+ * at the diagnostic steps inside them, and its closing two-buffer sweeps form
+ * the last piece).  A piece is identified by its length, whether it ends with
+ * a diagnostic sweep, the buffer parity it starts from, and for one-buffer
+ * pieces the sweep (push or local) it starts with.  The first time a piece is
+ * asked for its sweeps are launched
  * directly; the second time it is captured into a CUDA graph, which is
  * replayed from then on (up to 16 pieces are remembered per handle, least
  * recently used first out).  So repeated calls of one length -- a serving
