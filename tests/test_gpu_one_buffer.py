@@ -59,9 +59,11 @@ def test_one_buffer_equals_two_buffers(stream, prec, case):
         ref.step(n)
         lat.step(n)
         assert_same(state(ref), state(lat), (name, prec, n))
-    fa, fb = ref.fields(), lat.fields()
-    for k in fa:
-        assert np.array_equal(fa[k], fb[k]), (name, prec, k)
+        # every call closes over two buffers, so the fields are recomputed from the
+        # previous step's populations after calls of any length
+        fa, fb = ref.fields(), lat.fields()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), (name, prec, n, k)
     s = lbm.lbm_get_launch_stats(lat.h)
     assert s["sweeps_replayed"] > 0
 
