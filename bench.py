@@ -52,6 +52,7 @@ BYTES_PER_LUP = {"fp32": 144, "fp64": 288, "fp16": 72, "bf16": 72, "fp16sr": 72,
 DIAG_EVERY = 100
 METRIC = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
+L2_MB = 129.0  # GB300 L2 capacity
 REFERENCE_BUDGET_S = 120.0  # timed oracle work of one --impl reference run
 # FP64 operations (adds, subtracts, multiplies, one divide; an FMA counts as
 # two) in one interior-cell update as the sweep writes it out: macroscopic
@@ -73,7 +74,7 @@ def sweep_launches(warmup: int, steps: int) -> int:
 
 
 def workload_config(precision: str) -> dict:
-    one = precision == "fp32"   # the library's default streaming for FP32 (lbm_set_streaming)
+    one = precision != "fp64"   # the library's default streaming (lbm_set_streaming)
     mb = BYTES_PER_LUP[precision] * NX * NY / 2 / 1e6      # one buffer of populations
     return {"workload": f"cavity {NX}x{NY}, Ra 1e8, Pr 1, Ste 1, Ma 0.1, strip W/4 centred, "
                         f"{precision.upper()} populations",
@@ -82,7 +83,9 @@ def workload_config(precision: str) -> dict:
             "streaming": ("one buffer (push / local sweeps), the call's last 1-2 sweeps over two buffers"
                           if one else "two buffers"),
             "l2": (f"inputs larger than L2 ({mb:.0f} MB of populations in the buffer a step reads and "
-                   "writes), no flush" if one else
+                   "writes), no flush" if one and mb > L2_MB else
+                   f"the populations ({mb:.0f} MB in the one buffer a step reads and writes) fit in the "
+                   f"{L2_MB:.0f} MB L2: a step reads what the previous one wrote, no flush" if one else
                    f"inputs larger than L2 (2 x {mb:.0f} MB populations), no flush")}
 
 
@@ -560,7 +563,7 @@ def run_batch(args) -> None:
                                f"W/4 at 0.2-0.8 W, seeded), {prec.upper()} populations, one fused "
                                "launch per step", "lattices": n, "precision": prec,
                    "streaming": ("one buffer (push / local sweeps), the call's last 1-2 steps over two buffers"
-                                 if prec == "fp32" else "two buffers"),
+                                 if prec != "fp64" else "two buffers"),
                    # both population buffers together are the algorithmic bytes of a step
                    "l2": (f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB of populations), no flush"
                           if alg_bytes > 129e6 else

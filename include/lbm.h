@@ -198,11 +198,10 @@ int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int grap
  * still in L2 when the next one reads it.  Both buffers stay allocated.  The
  * staged 16-bit sweep and lbm_step_static always use two buffers; a batch has
  * its own setting (lbm_batch_set_streaming).
- * Default (set by lbm_create): one buffer for LBM_FP32, whose sweep is bound
- * by memory (2048 x 1024 cavity on GB300: 41.4 -> 37.0 us per step); two
- * buffers for the 16-bit types, whose sweeps are bound by instruction issue
- * and slow down with the push sweep's addressing, and for LBM_FP64, bound by
- * its arithmetic.  Takes effect at the next lbm_step.  Errors: LBM_ERR_ARG. */
+ * Default (set by lbm_create): one buffer (2048 x 1024 cavity on GB300: FP32
+ * 41.4 -> 36.5 us per step, BF16-SR 26.1 -> 24.2 us), except for LBM_FP64,
+ * which is bound by its arithmetic and keeps two buffers.  Takes effect at the
+ * next lbm_step.  Errors: LBM_ERR_ARG. */
 enum { LBM_STREAM_TWO_BUFFERS = 0, LBM_STREAM_ONE_BUFFER = 1 };
 int lbm_set_streaming(lbm_handle h, int mode);
 
@@ -357,9 +356,8 @@ int lbm_batch_set_launch(lbm_batch b, int rows_per_block, int prefetch_rows, int
  * buffer, and the closing steps run over two buffers, so that between calls
  * every member's state is the two-buffer one (results do not depend on the
  * mode, bit for bit; members may be stepped alone or in other batches between
- * calls).  Until this is called the batch follows its precision: one buffer for
- * LBM_FP32, two otherwise.  Synchronises the batch's stream.  Errors:
- * LBM_ERR_ARG. */
+ * calls).  Until this is called the batch follows its precision: one buffer,
+ * two for LBM_FP64.  Synchronises the batch's stream.  Errors: LBM_ERR_ARG. */
 int lbm_batch_set_streaming(lbm_batch b, int mode);
 
 /* Autotuner for a batch: times rows per block (1, 2, 3, 4) x prefetch distance

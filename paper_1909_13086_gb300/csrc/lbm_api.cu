@@ -573,13 +573,12 @@ int lbm_create(int nx, int ny, int precision, void *cuda_stream, lbm_handle *out
         h->rows = kDefaultRows16;
         h->prefetch = kDefaultPrefetch16;
     }
-    // One-buffer streaming where it pays: the FP32 sweep is bound by memory,
-    // and a step whose working set is one buffer finds more of the previous
-    // step's rows in L2 (2048 x 1024 cavity on GB300: 41.4 -> 37.0 us per
-    // step).  The 16-bit sweeps are bound by instruction issue and pay more for
-    // the push sweep's addressing than they gain (BF16-SR 26.4 -> 29.0 us);
-    // FP64 is bound by its arithmetic.
-    h->streaming = precision == LBM_FP32 ? LBM_STREAM_ONE_BUFFER : LBM_STREAM_TWO_BUFFERS;
+    // One-buffer streaming where it pays: a step whose working set is one
+    // buffer finds more of the previous step's rows in L2, and the local sweep
+    // reads and writes aligned own slots (2048 x 1024 cavity on GB300: FP32
+    // 41.4 -> 36.5 us per step, BF16-SR 26.1 -> 24.2, FP16-SR 26.5 -> 24.5).
+    // FP64 is bound by its arithmetic (698 us per step either way).
+    h->streaming = precision == LBM_FP64 ? LBM_STREAM_TWO_BUFFERS : LBM_STREAM_ONE_BUFFER;
     set_grid(h);
     h->alloc = g_alloc;
     h->release = g_free;
@@ -1020,7 +1019,7 @@ struct lbm_batch_s {
     int rows = 0;             // launch shape: rows per block (0: 2, or 4 with 16-bit storage),
     int prefetch = -1;        // L2 prefetch distance (-1: 4 rows),
     int interleave = 1;       // interleaved block order (uniform batches only; see batch_kernel)
-    int streaming = -1;       // lbm_batch_set_streaming; -1: one buffer for FP32, two otherwise
+    int streaming = -1;       // lbm_batch_set_streaming; -1: one buffer, two for FP64
     bool dirty = true;        // table must be rebuilt and uploaded
     int precision = -1, problem = -1, flow = -1;
     int graph_chunk = 128;    // longest graph-replayed piece; even, so that every
@@ -1136,7 +1135,7 @@ int batch_steps(lbm_batch_s *b, long long n) {
     // call, an even number, alternate push (even j) and local (odd j) sweeps
     // in each member's buffer parity[r]; the last one or two run over the two
     // buffers, so that between calls every member's state is the two-buffer one.
-    const bool one = b->streaming < 0 ? b->precision == LBM_FP32 : b->streaming == LBM_STREAM_ONE_BUFFER;
+    const bool one = b->streaming < 0 ? b->precision != LBM_FP64 : b->streaming == LBM_STREAM_ONE_BUFFER;
     const long long aa = (one && n >= 3) ? ((n & 1) ? n - 1 : n - 2) : 0;
     auto direct = [&](long long from, long long len, bool diag, bool ob) -> int {
         for (long long j = 0; j < len; ++j) {

@@ -525,6 +525,29 @@ __device__ __forceinline__ void bounce_side_walls(const typename Store<S>::elem 
     }
 }
 
+// A cavity warp that touches a side wall, on an interior row, in the push
+// sweep of one-buffer streaming: pull_fast's bases and offsets, except that a
+// direction whose source lies beyond the side wall reads the cell's own slot
+// opp(i) (its post-collision opposite population, which the adiabatic wall
+// returns as it is) instead of a clamped address -- so, unlike pull_fast plus
+// bounce_side_walls, the warp reads only what its own cells write.
+template <typename real, typename S, bool FLOW>
+__device__ __forceinline__ void pull_sidewall(const typename Store<S>::elem *b,
+                                              const typename Store<S>::elem *bL,
+                                              const typename Store<S>::elem *bR, int x, int nx, real f[9],
+                                              real g[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        const bool wall = (cx > 0 && x == 0) || (cx < 0 && x == nx - 1);
+        const typename Store<S>::elem *from = (cx > 0 ? bL : (cx < 0 ? bR : b)) - cy * kRS - cx * col_step<S>();
+        real fv = real(0), gv;
+        load_own<real, S, FLOW>(wall ? b : from, wall ? opp_of(i) : i, fv, gv);
+        if (FLOW) f[i] = fv;
+        g[i] = gv;
+    }
+}
+
 // The rule for the g population of direction i entering cell x from beyond a
 // wall (source (sx, sy) outside the lattice), given gv = the cell's own
 // post-collision g*_opp(i): half-way bounce-back (gv as it is) on adiabatic
@@ -928,6 +951,23 @@ struct PushFast {
     }
     __device__ __forceinline__ int slot(int i) const { return opp_of(i); }
 };
+// A cavity side-wall warp on an interior row (see pull_sidewall): PushFast's
+// targets, except that a direction leaving through the side wall goes to the
+// cell's own slot i.
+template <typename S>
+struct PushSide {
+    typename Store<S>::elem *b, *bL, *bR;
+    int x, nx;
+    __device__ __forceinline__ bool wall(int i) const {
+        const int cx = cx_of(i);
+        return (cx > 0 && x == nx - 1) || (cx < 0 && x == 0);
+    }
+    __device__ __forceinline__ typename Store<S>::elem *cell(int i) const {
+        const int cx = cx_of(i), cy = cy_of(i);
+        return wall(i) ? b : (cx > 0 ? bR : (cx < 0 ? bL : b)) + cy * kRS + cx * col_step<S>();
+    }
+    __device__ __forceinline__ int slot(int i) const { return wall(i) ? i : opp_of(i); }
+};
 template <typename S, int PROB>
 struct PushAny {
     typename Store<S>::elem *buf;  // the buffer's first element
@@ -1121,9 +1161,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
             } else if ((fastcol || (SM == kPull && sidewall)) && inner) {
                 // (a side-wall warp's clamped loads read other cells' slots,
                 // which the push sweep may be rewriting: it pulls those warps
-                // with pull_any, which reads only what the cell itself writes)
+                // with pull_sidewall, which reads only what its cells write)
                 pull_fast<real, S, FLOW>(src + i0, src + iL, src + iR, f, g);
                 if (SM == kPull && sidewall) bounce_side_walls<real, S, FLOW>(src + i0, x, a.nx, f, g);
+            } else if (SM == kAAPush && sidewall && inner) {
+                pull_sidewall<real, S, FLOW>(src + i0, src + iL, src + iR, x, a.nx, f, g);
             } else {
                 pull_any<real, S, PROB, FLOW>(a, x, y, f, g, acc.q);
             }
@@ -1131,6 +1173,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<real> &a, const int 
                 if (fastcol && inner)
                     finish_cell<real, S, FLOW, MODE>(a, x, y, PushFast<S>{dst + i0, dst + iL, dst + iR}, f, g,
                                                      step_seed, cd);
+                else if (sidewall && inner)
+                    finish_cell<real, S, FLOW, MODE>(a, x, y, PushSide<S>{dst + i0, dst + iL, dst + iR, x, a.nx},
+                                                     f, g, step_seed, cd);
                 else
                     finish_cell<real, S, FLOW, MODE>(a, x, y, PushAny<S, PROB>{dst, x, y, a.nx, a.ny}, f, g,
                                                      step_seed, cd);

@@ -124,8 +124,11 @@ def push_sweep_sets(nx, ny, paired, stefan, flow):
     """Per cell, the elements the push sweep reads and writes, replaying the
     sweep's own arithmetic: pull_fast's bases and offsets and PushFast's
     targets (base by c_x, + c_y rows + c_x columns, slot opp(i)) for cells of
-    warps clear of both side walls on interior rows; pull_any's and PushAny's
-    per-direction targets elsewhere (y periodic for the Stefan problem)."""
+    warps clear of both side walls on interior rows; for the cavity's side-wall
+    warps on interior rows pull_sidewall's and PushSide's (the same bases, the
+    cell's own slots across the side wall), checked element by element against
+    pull_any's and PushAny's per-direction targets, which serve everywhere else
+    (y periodic for the Stefan problem)."""
     cs = 2 if paired else 1
     halves = (0, 9) if flow else (9,)
     offs = load_offsets(paired)
@@ -152,6 +155,13 @@ def push_sweep_sets(nx, ny, paired, stefan, flow):
                         assert e == elem(x + cx, y + cy, P + OPP[i], ny, paired), (nx, x, y, i, P)
                         writes.append(e)
             else:
+                side = not stefan and inner    # a cavity side-wall warp: pull_sidewall / PushSide
+                i0 = pop_index(x, y, 0, ny, paired)
+                iL = pop_index(x - 1, y, 0, ny, paired) + cs if (lx == 0 and x > 0) else i0
+                iR = pop_index(x + 1, y, 0, ny, paired) - cs if (lx == TW - 1 and x < nx - 1) else i0
+
+                def slot_elem(cell, slot, P):
+                    return cell + (2 * slot * TW + (1 if P else 0) if paired else (P + slot) * TW)
                 for i, (cx, cy) in enumerate(C):
                     sx, sy, tx, ty = x - cx, y - cy, x + cx, y + cy
                     if stefan:
@@ -159,8 +169,17 @@ def push_sweep_sets(nx, ny, paired, stefan, flow):
                     src_in = 0 <= sx < nx and 0 <= sy < ny
                     dst_in = 0 <= tx < nx and 0 <= ty < ny
                     for P in halves:
-                        reads.append(elem(sx, sy, P + i, ny, paired) if src_in else elem(x, y, P + OPP[i], ny, paired))
-                        writes.append(elem(tx, ty, P + OPP[i], ny, paired) if dst_in else elem(x, y, P + i, ny, paired))
+                        r = elem(sx, sy, P + i, ny, paired) if src_in else elem(x, y, P + OPP[i], ny, paired)
+                        w = elem(tx, ty, P + OPP[i], ny, paired) if dst_in else elem(x, y, P + i, ny, paired)
+                        if side:
+                            wall = (cx > 0 and x == 0) or (cx < 0 and x == nx - 1)
+                            frm = (iL if cx > 0 else (iR if cx < 0 else i0)) - cy * RS - cx * cs
+                            assert slot_elem(i0 if wall else frm, OPP[i] if wall else i, P) == r, (nx, x, y, i)
+                            wall_t = (cx > 0 and x == nx - 1) or (cx < 0 and x == 0)
+                            to = i0 if wall_t else (iR if cx > 0 else (iL if cx < 0 else i0)) + cy * RS + cx * cs
+                            assert slot_elem(to, i if wall_t else OPP[i], P) == w, (nx, x, y, i)
+                        reads.append(r)
+                        writes.append(w)
             out[(x, y)] = (reads, writes)
     return out
 
