@@ -564,10 +564,15 @@ def run_batch(args) -> None:
                                "launch per step", "lattices": n, "precision": prec,
                    "streaming": ("one buffer (push / local sweeps), the call's last 1-2 steps over two buffers"
                                  if prec != "fp64" else "two buffers"),
-                   # both population buffers together are the algorithmic bytes of a step
-                   "l2": (f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB of populations), no flush"
-                          if alg_bytes > 129e6 else
-                          f"inputs fit in L2 ({alg_bytes / 1e6:.0f} MB of populations)"),
+                   # a step reads and writes every population once: half the algorithmic bytes
+                   # is the state; with two buffers the step touches twice that
+                   "l2": (f"inputs larger than L2 ({alg_bytes / 1e6:.0f} MB of populations in the two "
+                          "buffers), no flush" if prec == "fp64" else
+                          f"inputs larger than L2 ({alg_bytes / 2e6:.0f} MB of populations in the buffer "
+                          "a step reads and writes), no flush" if alg_bytes / 2 > L2_MB * 1e6 else
+                          f"the populations ({alg_bytes / 2e6:.0f} MB in the one buffer a step reads and "
+                          f"writes) fit in the {L2_MB:.0f} MB L2: a step reads what the previous one "
+                          "wrote, no flush"),
                    "launch": ({"rows": tuned["rows"], "prefetch": tuned["prefetch"],
                                "interleave": tuned["interleave"], "by": "lbm_batch_autotune"}
                               if tuned else "default")},
