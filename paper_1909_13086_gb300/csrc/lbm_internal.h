@@ -64,9 +64,10 @@ struct DevRecord {
     double timeout;   // 1 once a bounded device wait ran out (staged sweep)
 };
 
-// Arguments of every lattice kernel, passed by value.
+// Arguments of every lattice kernel, passed by value.  16-byte aligned, so
+// that a batch entry's argument sets start on 16-byte pieces.
 template <typename real>
-struct SweepArgs {
+struct alignas(16) SweepArgs {
     // Population buffers, tile-major, of the storage type S the launcher was
     // instantiated with (float, double, __half or __nv_bfloat16).
     const void *src;       // populations of the previous step

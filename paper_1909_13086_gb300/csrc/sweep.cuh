@@ -32,6 +32,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <type_traits>
@@ -1482,12 +1483,24 @@ __device__ __forceinline__ int batch_find(const int *starts, int n, int b) {
 // SM: kPull, or a sweep of one-buffer streaming (kAAPush at even j, kAALocal
 // at odd j): the member's arguments for its buffer parity[r] are then used
 // with the destination set to the source and the parity word to
-// parity[r] ^ (j & 1), patched in the shared-memory copy.
+// parity[r] ^ (j & 1), patched in the 16-byte pieces of the shared-memory
+// copy that hold them, as they are copied.
+template <typename real>
+struct EntryLayout {
+    static constexpr unsigned kArgs = sizeof(SweepArgs<real>);
+    static constexpr unsigned kSrc = offsetof(SweepArgs<real>, src);
+    static constexpr unsigned kDst = offsetof(SweepArgs<real>, dst);
+    static constexpr unsigned kPar = offsetof(SweepArgs<real>, parity);
+    static_assert(kArgs % 16 == 0 && kSrc % 16 == 0 && kDst == kSrc + 8,
+                  "src and dst of each argument set share one 16-byte piece");
+    static_assert(offsetof(BatchEntry<real>, a) == 0, "the argument sets open the entry");
+};
 template <typename real, typename S, int PROB, bool FLOW, int MODE, int SM = kPull>
 __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
     batch_kernel(const BatchEntry<real> *entries, const int *starts, const int *parity, int n,
                  int uniform, int interleave, int j) {
     static_assert(sizeof(BatchEntry<real>) % 16 == 0, "entries are copied in 16-byte pieces");
+    using L = EntryLayout<real>;
     __shared__ double sh[32 * 4];
     __shared__ __align__(16) unsigned char entry_sh[sizeof(BatchEntry<real>)];
     __shared__ int meta[2];
@@ -1504,20 +1517,34 @@ __global__ void __launch_bounds__(kTW, sizeof(real) == 4 ? 1024 / kTW : 1)
         __syncthreads();
         r = meta[0];
     }
+    // every thread reads the parity word (one broadcast load, issued with the
+    // copy's loads), so the pieces are patched on the way and one barrier
+    // publishes the copy
+    const int p = __ldg(parity + r) ^ (SM == kPull ? (j & 1) : 0);
     const int4 *s4 = reinterpret_cast<const int4 *>(entries + r);
     int4 *d4 = reinterpret_cast<int4 *>(entry_sh);
-    for (unsigned k = threadIdx.x; k < sizeof(BatchEntry<real>) / 16; k += blockDim.x)
-        d4[k] = __ldg(s4 + k);
-    if (threadIdx.x == 0) meta[1] = __ldg(parity + r) ^ (SM == kPull ? (j & 1) : 0);
-    __syncthreads();
-    if constexpr (SM != kPull) {
-        if (threadIdx.x == 0) {
-            SweepArgs<real> &x = reinterpret_cast<BatchEntry<real> *>(entry_sh)->a[meta[1]];
-            x.dst = const_cast<void *>(x.src);
-            x.parity = meta[1] ^ (j & 1);
+    for (unsigned k = threadIdx.x; k < sizeof(BatchEntry<real>) / 16; k += blockDim.x) {
+        int4 v = __ldg(s4 + k);
+        if constexpr (SM != kPull) {
+            const unsigned base = (unsigned)p * L::kArgs;  // a[p] within the entry
+            if (k == (base + L::kSrc) / 16) {
+                v.z = v.x;  // dst = src (the same 8 bytes)
+                v.w = v.y;
+            }
+            if (k == (base + L::kPar) / 16) {
+                const int par = p ^ (j & 1);
+                switch ((L::kPar % 16) / 4) {
+                    case 0: v.x = par; break;
+                    case 1: v.y = par; break;
+                    case 2: v.z = par; break;
+                    default: v.w = par; break;
+                }
+            }
         }
-        __syncthreads();
+        d4[k] = v;
     }
+    if (threadIdx.x == 0) meta[1] = p;  // read back after the barrier: no register held across it
+    __syncthreads();
     pdl_wait();
     const BatchEntry<real> &e = *reinterpret_cast<const BatchEntry<real> *>(entry_sh);
     const SweepArgs<real> &a = e.a[meta[1]];
