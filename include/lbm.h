@@ -181,8 +181,7 @@ int lbm_set_diag_every(lbm_handle h, long long k);
 int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int graph_chunk);
 
 /* How lbm_step moves the populations from one step to the next.
- * LBM_STREAM_TWO_BUFFERS (the default): every sweep pulls from one buffer into
- * the other.  LBM_STREAM_ONE_BUFFER: all but the last one or two sweeps of a
+ * LBM_STREAM_TWO_BUFFERS: every sweep pulls from one buffer into the other.  LBM_STREAM_ONE_BUFFER: all but the last one or two sweeps of a
  * call work in place in one buffer, alternating two sweeps (the AA pattern of
  * Bailey et al., "Accelerating lattice Boltzmann fluid flow simulations using
  * graphics processors", 2009): a push sweep that pulls as usual and puts
@@ -199,7 +198,7 @@ int lbm_set_launch(lbm_handle h, int rows_per_block, int prefetch_rows, int grap
  * staged 16-bit sweep and lbm_step_static always use two buffers; a batch has
  * its own setting (lbm_batch_set_streaming).
  * Default (set by lbm_create): one buffer (2048 x 1024 cavity on GB300: FP32
- * 41.4 -> 36.5 us per step, BF16-SR 26.1 -> 24.2 us), except for LBM_FP64,
+ * 41.4 -> 36.6 us per step, BF16-SR 26.1 -> 24.4 us), except for LBM_FP64,
  * which is bound by its arithmetic and keeps two buffers.  Takes effect at the
  * next lbm_step.  Errors: LBM_ERR_ARG. */
 enum { LBM_STREAM_TWO_BUFFERS = 0, LBM_STREAM_ONE_BUFFER = 1 };
