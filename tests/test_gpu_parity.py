@@ -3,9 +3,10 @@
 Bars: FP64 GPU path within 1e-12 of the oracle relative to each field's (or
 population plane set's) largest magnitude; FP32 path within 1e-5 max-abs in T
 and f_l after 1000 steps.  Sizes: the 64 x 32 cavity, ragged lattices that do
-not fill a 256-wide block, the 1024 x 4 Stefan problem, and sampled cells of
-the full 2048 x 1024 production cavity in the launch configuration the
-benchmark times.
+not fill a 256-wide block, the 1024 x 4 Stefan problem, and the full 2048 x
+1024 production cavity in the launch configuration the benchmark times
+(sampled cells after a pull sweep; every cell after a call of one-buffer
+sweeps).
 """
 import math
 
@@ -426,6 +427,40 @@ def test_full_size_sampled_parity_fp32(orc, stream):
         assert np.abs(fo - fnew[:, y, x]).max() <= 1e-5, (x, y)
         for k, name in enumerate(FIELDS):
             assert abs(m[k] - F[name][y, x]) <= 1e-5, (x, y, name)
+
+
+@pytest.mark.parametrize("calls,n", [(1, 5), (3, 100)])
+def test_full_size_one_buffer_sweeps_vs_oracle_fp32(orc, stream, calls, n):
+    """2048 x 1024 production cavity, FP32, in the benchmark's streaming and
+    launch shape (diagnostics every 100th step): from the GPU's own populations
+    after 100 steps, `calls` calls of n steps -- 5: push, local, push, local
+    sweeps in one buffer, then a pull sweep into the other; three calls of
+    100: the same 100-step piece ending in a diagnostic sweep, launched
+    directly, then from its graph -- against the oracle's steps from the same
+    populations, every population of every cell, and the fields."""
+    nx, ny, p = workloads.cavity_2048x1024()
+    lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    lbm.lbm_set_streaming(lat.h, lbm.LBM_STREAM_ONE_BUFFER)  # the FP32 default, stated
+    lbm.lbm_set_diag_every(lat.h, 100)
+    lat.step(100)
+    f0, g0, s0 = lat.populations()
+    ref = orc.Oracle(nx, ny, threads=8, **p)
+    ref.set_populations(f0, g0, s0)
+    del f0, g0
+    for _ in range(calls):
+        lat.step(n)
+    if calls > 2:
+        assert lbm.lbm_get_launch_stats(lat.h)["sweeps_replayed"] > 0
+    ref.step(calls * n)
+    f1, g1, s1 = lat.populations()
+    fo, go = ref.populations()
+    assert s1 == s0 + calls * n
+    assert np.abs(g1 - go).max() <= 1e-5
+    assert np.abs(f1 - fo).max() <= 1e-5
+    del f1, g1, fo, go
+    F, Fo = lat.fields(), ref.fields()
+    for name in ("T", "fl", "ux", "uy"):
+        assert np.abs(F[name] - Fo[name]).max() <= 1e-5, name
 
 
 def test_full_size_budget_and_bounds_fp32(stream):
