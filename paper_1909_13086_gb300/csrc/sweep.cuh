@@ -293,22 +293,27 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // With X = B2xx, Y = B2yy, Z = B2xy, S = X + Y and Q_i = c_i c_i - I/3, the
 // products w_i * 9/2 Q_i:B2 are -2S/3 (rest), X/3 - Y/6 (+-x), Y/3 - X/6
 // (+-y), S/12 + Z/4 (diagonals 5, 7) and S/12 - Z/4 (6, 8); w_i * 3 c_i.B1 is
-// +-B1x/3, +-B1y/3, +-(B1x + B1y)/12 and +-(B1y - B1x)/12.
+// +-B1x/3, +-B1y/3, +-(B1x + B1y)/12 and +-(B1y - B1x)/12.  In FP32 the
+// rounded weights sum to 1 + 7.45e-9, which would add k0 B0 7.45e-9 to every
+// cell's sum each step (a steady growth of the FP32 density); the rest weight's
+// share is therefore taken as B0 - 4 (w1 B0 + w5 B0), so that the shares sum
+// to B0 up to rounding.  FP64's weights sum to 1 within 1e-16 and keep w0 B0.
 template <typename real>
 __device__ __forceinline__ void emit(real p[9], real a, real B0, real B1x, real B1y, real B2xx,
                                      real B2xy, real B2yy) {
     const real third = real(1) / real(3), sixth = real(1) / real(6), twelfth = real(1) / real(12);
     const real w0 = real(4) / real(9), w1 = real(1) / real(9), w5 = real(1) / real(36);
     const real S = B2xx + B2yy;
-    p[0] = a * p[0] + (w0 * B0 - (real(2) / real(3)) * S);
-    const real W1 = w1 * B0;
+    const real W1 = w1 * B0, W5 = w5 * B0;
+    const real W0 = sizeof(real) == 4 ? B0 - real(4) * (W1 + W5) : w0 * B0;
+    p[0] = a * p[0] + (W0 - (real(2) / real(3)) * S);
     const real e13 = W1 + third * B2xx - sixth * B2yy, t1 = third * B1x;
     p[1] = a * p[1] + (e13 + t1);
     p[3] = a * p[3] + (e13 - t1);
     const real e24 = W1 + third * B2yy - sixth * B2xx, t2 = third * B1y;
     p[2] = a * p[2] + (e24 + t2);
     p[4] = a * p[4] + (e24 - t2);
-    const real e5 = w5 * B0 + twelfth * S, z4 = real(0.25) * B2xy;
+    const real e5 = W5 + twelfth * S, z4 = real(0.25) * B2xy;
     const real e57 = e5 + z4, t5 = twelfth * (B1x + B1y);
     p[5] = a * p[5] + (e57 + t5);
     p[7] = a * p[7] + (e57 - t5);
@@ -418,6 +423,14 @@ __device__ __forceinline__ Macro<real> cell_update(const SweepArgs<real> &a, rea
         const real k0 = a.k0f;
         emit(f, real(1) - k0, k0 * R0, k0 * rux - A1x, k0 * ruy - A1y, k0 * rxx - A2xx,
              k0 * rxy - A2xy, k0 * ryy - A2yy);
+        // FP32 storage: the collision conserves mass, sum f*_i = sum f_i, and
+        // the rest population is taken from that invariant, so that the
+        // rounding of the nine emitted values leaves no drift in the density
+        // (other rounding biases of the emitted values add ~4e-9 per step in
+        // a convecting cavity).  16-bit storage rounds f*_i stochastically on
+        // store, which is unbiased.
+        if constexpr (!kDev && sizeof(real) == 4)
+            f[0] = fs - (((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
     }
     return m;
 }

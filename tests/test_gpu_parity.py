@@ -463,6 +463,20 @@ def test_full_size_one_buffer_sweeps_vs_oracle_fp32(orc, stream, calls, n):
         assert np.abs(F[name] - Fo[name]).max() <= 1e-5, name
 
 
+def test_fp32_mass_conserved_over_a_long_run(stream):
+    """The closed cavity conserves mass (Eq. 2's flow analogue: the collision
+    keeps sum f_i, bounce-back walls return what leaves).  In FP32 the rounded
+    D2Q9 weights sum to 1 + 7.45e-9; had each collision carried that excess,
+    the 64 x 32 cavity's mean density would have grown by ~4e-4 over 5e4
+    steps.  It must stay within 3e-5 of 1."""
+    nx, ny, p = workloads.cavity_64x32()
+    lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
+    assert abs(lat.fields()["rho"].mean() - 1.0) <= 1e-7
+    lat.step(50000)
+    assert lat.diagnostics()["nan_flag"] == 0
+    assert abs(lat.fields()["rho"].mean() - 1.0) <= 3e-5
+
+
 def test_full_size_budget_and_bounds_fp32(stream):
     nx, ny, p = workloads.cavity_2048x1024()
     lat = lbm.Lattice(nx, ny, p, precision="fp32", stream=stream)
