@@ -95,6 +95,18 @@ def test_committed_profiles_carry_hash_and_traffic():
             assert "kernel_source_sha256:" in text, f
 
 
+def test_workload_config_states_the_streaming_and_the_l2_footprint():
+    # one buffer for every storage type but FP64; the note says whether the
+    # buffer a step reads and writes exceeds the 129 MB L2 (FP32: 151 MB) or
+    # fits in it (16-bit: 75 MB), and FP64's two buffers (604 MB) exceed it
+    fp32, bf16, fp64 = (bench.workload_config(p) for p in ("fp32", "bf16sr", "fp64"))
+    assert fp32["streaming"].startswith("one buffer") and bf16["streaming"].startswith("one buffer")
+    assert fp64["streaming"] == "two buffers"
+    assert fp32["l2"].startswith("inputs larger than L2 (151 MB")
+    assert "fit in the 129 MB L2" in bf16["l2"] and "(75 MB" in bf16["l2"]
+    assert fp64["l2"].startswith("inputs larger than L2 (2 x 302 MB")
+
+
 def test_measured_peak_falls_back(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_peak_gbs() == (bench.FALLBACK_HBM_GBS, "fallback")
